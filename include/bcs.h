@@ -1,0 +1,213 @@
+/*
+ * bcs.h -- C ABI of the GB300 (sm_103a) pipelined BiCGSafe solver library.
+ *
+ * Solves nonsymmetric sparse A x = b with the single-reduction ssBiCGSafe2
+ * method and its pipelined variants, after Huynh & Suito, "Communication-
+ * hiding pipelined BiCGSafe methods for solving large linear systems"
+ * (arXiv 2108.10591):
+ *   BCS_SSBICGSAFE2    Section 2, Algorithm 3 (one phase of nine inner products)
+ *   BCS_P_BICGSAFE     Section 3, Algorithm 4 (the inner-product phase of
+ *                      iteration i overlaps the product A s_i; Eqs. (s)-(g))
+ *   BCS_P_BICGSAFE_RR  Section 4, Algorithm 5 (residual replacement every m
+ *                      iterations while i < M)
+ * Every solve runs as one persistent CUDA kernel; the scalar recurrence
+ * (alpha, beta, zeta, eta and the stop test) stays on the device.
+ *
+ * Conventions for every entry point:
+ *  - Return value: BCS_OK (0) or a BCS_* status below; no exceptions, no
+ *    process exit.  BCS_NOT_CONVERGED (positive) still leaves a valid best
+ *    iterate in x.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the current device (for example a PyTorch tensor's
+ *    data_ptr()).  The caller owns every buffer it passes; the library owns
+ *    the matrix and solver objects and frees them in bcs_matrix_free /
+ *    bcs_solver_destroy.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Objects are not thread-safe; a matrix may be shared by several solvers
+ *    as long as it outlives them.
+ *  - Vectors are FP64, length n, in the original row order, contiguous.
+ */
+#ifndef BCS_H
+#define BCS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcs_matrix_s* bcs_matrix;
+typedef struct bcs_solver_s* bcs_solver;
+
+/* Methods (the paper's Algorithms 3, 4 and 5). */
+enum { BCS_SSBICGSAFE2 = 0, BCS_P_BICGSAFE = 1, BCS_P_BICGSAFE_RR = 2 };
+
+/* Precision of a solve.  BCS_FP64: vectors, matrix and arithmetic in FP64
+ * (the paper's setting, Section 5).  BCS_FP32_REFINE / BCS_BF16MAT_REFINE:
+ * inner solves with FP32 vectors and an FP32 / BF16 copy of the matrix
+ * values, FP64 inner-product accumulation and FP64 scalars, wrapped in FP64
+ * iterative refinement (r = b - A x with the FP64 matrix, x += d in FP64).
+ * The paper has no counterpart of the two refinement modes. */
+enum { BCS_FP64 = 0, BCS_FP32_REFINE = 1, BCS_BF16MAT_REFINE = 2 };
+
+/* Matrix layouts held on the device (bit mask for bcs_csr_upload). */
+enum { BCS_LAYOUT_CSR = 1, BCS_LAYOUT_SELL = 2 };
+/* Value copies held on the device (bit mask; FP64 is always kept). */
+enum { BCS_STORE_F64 = 1, BCS_STORE_F32 = 2, BCS_STORE_BF16 = 4 };
+
+/* Status codes. */
+enum {
+    BCS_OK = 0,
+    BCS_NOT_CONVERGED = 1,  /* maxit (or max_outer) reached; x holds the last iterate */
+    BCS_ERR_ARG = -1,       /* invalid argument or invalid CSR (see bcs_csr_upload) */
+    BCS_ERR_CUDA = -2,      /* a CUDA call failed (includes no device) */
+    BCS_ERR_BREAKDOWN = -3, /* zero denominator g+beta*h, zeta*f or (s,s) before convergence */
+    BCS_ERR_TIMEOUT = -4,   /* a grid barrier waited past the spin budget */
+    BCS_ERR_NONFINITE = -5, /* NaN or Inf in the scalar recurrence */
+    BCS_ERR_OOM = -6        /* device allocation failed */
+};
+
+typedef struct {
+    int rr_m;             /* Alg. 5 replacement epoch m (default 100; Section 5.2 uses 100 and 96) */
+    int rr_M;             /* Alg. 5 replacement limit M: replace only while i < M (default: maxit) */
+    int precision;        /* BCS_FP64 (default) | BCS_FP32_REFINE | BCS_BF16MAT_REFINE */
+    double inner_tol;     /* refinement modes: inner stop at ||r_inner|| <= inner_tol*||r_outer|| (default 1e-3) */
+    int max_outer;        /* outer steps: true-residual checks / restarts / refinement steps (default 30) */
+    int history_len;      /* capacity of the residual history (default 4096 entries) */
+    int layout;           /* BCS_LAYOUT_CSR (default) or BCS_LAYOUT_SELL; must have been uploaded */
+    int threads_per_row;  /* CSR only: 1,2,4,8,16 or 32 lanes per row; 0 = chosen from the row lengths */
+    int ctas_per_sm;      /* 0 = chosen by occupancy; otherwise 1..8 */
+    int max_ctas;         /* 0 = no cap; otherwise an upper bound on the grid size */
+    double spin_budget_ms;/* per grid-barrier wait before BCS_ERR_TIMEOUT (default 2000 ms) */
+} bcs_options;
+
+typedef struct {
+    int status;               /* BCS_* */
+    int iterations;           /* total iterations over all inner runs (the paper's i at the stop) */
+    int outer_steps;          /* true-residual evaluations (1 = converged on the first check) */
+    int rr_steps;             /* residual replacements performed (Alg. 5) */
+    int fallbacks;            /* iterations whose zeta, eta fell back to the i = 0 formulas */
+    double rel_res_recursive; /* sqrt(r_i)/||r_0|| at the last stop test */
+    double rel_res_true;      /* ||b - A x||_2 / ||b - A x_0||_2 in FP64 at exit */
+    double r0_norm;           /* ||b - A x_0||_2 */
+    double seconds;           /* device time of the solve (CUDA events) */
+} bcs_result;
+
+/* Fill *opt with the defaults listed above. */
+void bcs_options_default(bcs_options* opt);
+
+/*
+ * Copy a CSR matrix (host arrays) to the device and build the requested
+ * layouts and value copies there.  Defines A of "Ax = b" (Section 2).
+ *   n, nnz      rows (= columns) and nonzeros; 0 <= n, nnz < 2^31.
+ *   rowptr      host int64[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = nnz.
+ *   col         host int32[nnz], 0 <= col < n, strictly ascending within a row.
+ *   val         host double[nnz].
+ *   layouts     BCS_LAYOUT_CSR and/or BCS_LAYOUT_SELL.
+ *   sell_C      SELL slice height; must be 32 (one warp per slice).
+ *   sell_sigma  SELL sorting window, a positive multiple of sell_C (<= 4096).
+ *               SELL-C-sigma: rows sorted by length, descending and stable,
+ *               inside windows of sigma rows; slices stored column-major and
+ *               padded with value 0 and the padded row's own index.
+ *   stores      extra value copies (BCS_STORE_F32 rounds to nearest,
+ *               BCS_STORE_BF16 rounds to nearest even); FP64 is always kept.
+ * The CSR is validated on the device; any violation returns BCS_ERR_ARG
+ * without fixing the input.  The library owns the returned matrix.
+ */
+int bcs_csr_upload(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                   const double* val, int layouts, int sell_C, int sell_sigma, int stores,
+                   void* stream, bcs_matrix* out);
+
+/* Sizes of an uploaded matrix (any pointer may be NULL). */
+int bcs_matrix_info(bcs_matrix A, int64_t* n, int64_t* nnz, int64_t* sell_padded, int* layouts, int* stores);
+
+/*
+ * Copy the device-side format arrays back to host buffers (for bit-exact
+ * checks of the format build).  Any pointer may be NULL.
+ *   CSR : rowptr int32[n+1], col int32[nnz], val64 double[nnz], val32 float[nnz],
+ *         valbf16 uint16[nnz] (BF16 bit patterns).
+ *   SELL: perm int32[n] (original row at permuted position p), slice_ptr
+ *         int64[n/32+1] (element offsets), scol int32[padded] (permuted
+ *         column indices), sval64 double[padded].
+ * Returns BCS_ERR_ARG if a requested layout or store is absent.
+ */
+int bcs_matrix_export(bcs_matrix A, int32_t* rowptr, int32_t* col, double* val64, float* val32,
+                      uint16_t* valbf16, int32_t* perm, int64_t* slice_ptr, int32_t* scol,
+                      double* sval64);
+
+/*
+ * y = A x on the device (the "MV" of Section 3 and Table 1).
+ *   layout  BCS_LAYOUT_CSR or BCS_LAYOUT_SELL (must be uploaded).
+ *   store   BCS_STORE_F64 / F32 / BF16: which value copy to use.
+ *   x, y    device vectors of n elements in original row order, FP64 when
+ *           vec_f32 == 0, FP32 otherwise; x and y must not overlap.
+ *   threads_per_row  CSR lanes per row (1,2,4,8,16,32; 0 = automatic).
+ * Rows are summed with fused multiply-adds; with one lane per row (and for
+ * SELL) in storage order.  Asynchronous on stream.
+ */
+int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int vec_f32,
+             int threads_per_row, void* stream);
+
+/* Free a matrix (NULL is ignored).  Waits for the device first. */
+void bcs_matrix_free(bcs_matrix A);
+
+/*
+ * Create a solver for A (Algorithm 3, 4 or 5 by kind).
+ *   tol    epsilon of the stop test ||r_i|| <= eps ||r_0|| (Section 5; the
+ *          paper uses 1e-8).  At recursive convergence the FP64 true residual
+ *          is checked against the same bound and the method restarts from x
+ *          while it is above (at most max_outer - 1 restarts).
+ *   maxit  iteration limit over all inner runs (the paper uses 1e4).
+ *   opt    NULL for defaults.
+ * Allocates the Krylov workspace on the device (about 16 n-vectors).
+ */
+int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_options* opt,
+                      bcs_solver* out);
+
+/*
+ * Solve A x = b.  b_dev: device double[n]; x_dev: device double[n], x_0 on
+ * entry (the paper's experiments use x_0 = 0), the solution on exit.  Fills
+ * *res (may be NULL).  Synchronises the stream before returning.
+ */
+int bcs_solve(bcs_solver s, const double* b_dev, double* x_dev, bcs_result* res, void* stream);
+
+/*
+ * Same as bcs_solve with host buffers: copies b and x_0 to the device, solves
+ * and copies x back, all on stream (end-to-end entry point).
+ */
+int bcs_solve_host(bcs_solver s, const double* b_host, double* x_host, bcs_result* res, void* stream);
+
+/*
+ * Relative recursive residuals sqrt(r_i)/||r_0|| of the last solve, one per
+ * evaluated stop test (all inner runs), and the scalars alpha, beta, zeta,
+ * eta of the first inner run (4 per iteration).  out/scal may be NULL;
+ * *len receives the number of entries available (capped by history_len).
+ */
+int bcs_get_history(bcs_solver s, double* out, int cap, int* len);
+int bcs_get_scalars(bcs_solver s, double* out, int cap, int* len);
+
+/* Free a solver (NULL is ignored). */
+void bcs_solver_destroy(bcs_solver s);
+
+/*
+ * Solve nsys independent systems A[k] x[k] = b[k] in one persistent launch
+ * (no counterpart in the paper: it solves one system at a time).  Each
+ * system is handled by one thread-block cluster, taken from a work list in
+ * decreasing size; a system retires as soon as it converges.
+ *   A      host array of nsys matrix handles (CSR layout).
+ *   b, x   host arrays of nsys device pointers (double[n_k] each).
+ *   res    host array of nsys results (may be NULL).
+ *   kind, tol, maxit, opt as for bcs_solver_create (opt->precision selects
+ *   FP64 or FP32 + FP64 refinement; history is not recorded).
+ * Synchronises the stream before returning.  Returns the worst status.
+ */
+int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int maxit,
+                      const bcs_options* opt, const double* const* b, double* const* x,
+                      bcs_result* res, void* stream);
+
+/* Static English name of a status code. */
+const char* bcs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCS_H */
