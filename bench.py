@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark: time to a 1e-10 relative residual on the 3D convection-diffusion
+workload (128^3, 7-point first-order upwind, n = 2,097,152, nnz = 14,581,760),
+FP64, p-BiCGSafe (Alg. 4) with the FP64 true-residual check; plain
+ssBiCGSafe2 (Alg. 3) and the mixed-precision pipelined solve are measured
+beside it on the same system.
+
+One step = one complete solve from x_0 = 0 to ||b - A x|| <= 1e-10 ||b||
+(one persistent kernel launch).  `value` = solves/s over all ranks with
+inputs resident in HBM; `e2e` = the same through bcs_solve_host (host b, x;
+copies inside the timed region).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-10 rel. residual, pipelined vs plain; HBM GB/s per iter; solves/s"
+WORKLOAD = "cd3d_128"
+HBM_PEAK_FALLBACK = 6800.0
+SMS = 152
+DFMA_PER_CLK_SM = 2          # GB300: FP64 FMA issue rate per SM per clock
+SM_MAX_MHZ = 2070.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": HBM_PEAK_FALLBACK}, "fallback"
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kind", default="p-BiCGSafe")
+    ap.add_argument("--tpr", type=int, default=0, help="CSR lanes per row (0 = library default)")
+    ap.add_argument("--layout", default="csr")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain / mixed side measurements")
+    ap.add_argument("--cpu-iters", type=int, default=30, help="oracle iterations in the CPU sample")
+    ap.add_argument("--size", type=int, default=128, help="grid side k of the k^3 system (128 = the benchmark)")
+    ap.add_argument("--maxit", type=int, default=10000, help="iteration limit (smaller for profiling runs)")
+    return ap.parse_args()
+
+
+def make_workload(k=128):
+    import workloads as W
+    A = W.cd3d_upwind(k, 50.0)
+    b = W.rhs_ones(A)
+    return A, b
+
+
+# ---- algorithmic work per solve ---------------------------------------------------------
+
+def flops_per_iter(kind, n, nnz):
+    """Table 1: two SpMVs (2 flops per nonzero each), the alpha*x and x+y counts per row
+    (26 + 22 for p-BiCGSafe, 16 + 14 for ssBiCGSafe2) and nine inner products (2n each)."""
+    ax, xy = (16, 14) if kind == "ssBiCGSafe2" else (26, 22)
+    return 2 * 2 * nnz + (ax + xy) * n + 9 * 2 * n
+
+
+def bytes_per_iter(kind, n, nnz, vbytes=8, mbytes=8):
+    """Algorithmic HBM bytes of one iteration: two passes over the CSR matrix
+    (values, int32 columns and row pointers) plus V + 2 vector passes (the two
+    SpMV inputs read once each), V = 25 (p-BiCGSafe: 11 state vectors read and
+    written, r* read, As written and re-read... lower bound) or 20 (ssBiCGSafe2)."""
+    V = 20 if kind == "ssBiCGSafe2" else 25
+    matrix = nnz * (mbytes + 4) + 4 * (n + 1)
+    return 2 * matrix + (V + 2) * n * vbytes
+
+
+def solve_work(kind, n, nnz, iters, outer, vbytes=8, mbytes=8):
+    f = iters * flops_per_iter(kind, n, nnz) + outer * (2 * nnz + 4 * n)
+    b = iters * bytes_per_iter(kind, n, nnz, vbytes, mbytes) + outer * (nnz * 12 + 4 * n * 8)
+    if kind != "ssBiCGSafe2":
+        f += outer * 2 * nnz
+        b += outer * (nnz * (mbytes + 4) + 2 * n * vbytes)
+    return f, b
+
+
+# ---- clocks ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons)}
+
+
+# ---- the CPU oracle baseline ---------------------------------------------------------------
+
+def cpu_sample(A, b, kind, iters):
+    """Time `iters` iterations of the CPU oracle (single thread) on the full system."""
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    o = oracle.solve(A, b, kind=kind, tol=0.0, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt, o
+
+
+def reference_arm(a):
+    A, b = make_workload()
+    kind = a.kind
+    iters_full = 370  # iterations of one full p-BiCGSafe solve of this system (oracle, measured once)
+    per = max(2, min(a.cpu_iters, 20))
+    times = []
+    for s in range(a.warmup + a.steps):
+        dt, _ = cpu_sample(A, b, kind, per)
+        if s >= a.warmup:
+            times.append(dt)
+    sec_per_iter = sum(times) / (len(times) * per)
+    solve_s = sec_per_iter * iters_full
+    val = 1.0 / solve_s
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "kind": kind, "precision": "fp64", "tol": 1e-10},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: %d iterations of the single-threaded FP64 oracle on the full "
+                                       "system, scaled to one solve by %d iterations" % (per, iters_full)},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm ---------------------------------------------------------------------------------
+
+def main():
+    a = args_parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if rank == 0:
+            reference_arm(a)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import paper_2108_10591_gb300 as bcs
+
+    A, b = make_workload(a.size)
+    n, nnz = A.n, A.nnz
+    layouts = bcs.LAYOUT_CSR | (bcs.LAYOUT_SELL if a.layout == "sell" else 0)
+    M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32)
+    stream = torch.cuda.current_stream()
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    solvers = {}
+
+    def get_solver(kind, precision="fp64"):
+        key = (kind, precision)
+        if key not in solvers:
+            solvers[key] = bcs.solver_create(M, kind, tol=1e-10, maxit=a.maxit, precision=precision,
+                                             threads_per_row=a.tpr, layout=a.layout, max_outer=30)
+        return solvers[key]
+
+    def run(kind, precision, steps, warmup, clocks=None):
+        S = get_solver(kind, precision)
+        for _ in range(warmup):
+            xd.zero_()
+            bcs.solve(S, bd, xd, stream=stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        results = []
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            xd.zero_()
+            ev[2 * k].record(stream)
+            results.append(bcs.solve(S, bd, xd, stream=stream))
+            ev[2 * k + 1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        total_ms = t0.elapsed_time(t1)
+        per = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]
+        return total_ms, per, results
+
+    with Clocks(local) as ck:
+        total_ms, per, results = run(a.kind, "fp64", a.steps, a.warmup)
+    clocks = ck.summary()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    r0 = results[-1]
+    ok = all(r["status"] == 0 and r["rel_res_true"] <= 1e-10 for r in results)
+    iters, outer = r0["iterations"], r0["outer_steps"]
+    kernel_ms = statistics.mean(per)
+
+    # roofline of the solve kernel (the only kernel in the step)
+    peaks, peak_src = measured_peaks()
+    f, by = solve_work(a.kind, n, nnz, iters, outer)
+    fp64_peak = SMS * DFMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6
+    achieved_tf = f / (kernel_ms * 1e-3) / 1e12
+    achieved_gbs = by / (kernel_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved_tf / (fp64_peak / 1e12), "traffic": None,
+                "kernel": "solve_kernel<double,double,CSR>", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 "
+                "flop x 2070 MHz (FP64 ALU; the kernel's binding unit on GB300)",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                        "peak_source": peak_src}}
+
+    # end to end through the public API with host buffers
+    bh = torch.from_numpy(b).pin_memory().numpy()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    S = get_solver(a.kind, "fp64")
+    for _ in range(max(1, a.warmup)):
+        xh[:] = 0.0
+        bcs.solve_host(S, bh, xh, stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e2e_steps = max(3, a.steps // 2)
+    for _ in range(e2e_steps):
+        xh[:] = 0.0
+        bcs.solve_host(S, bh, xh, stream=stream)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    extras = {}
+    if not a.no_extras:
+        for kind, prec in [("ssBiCGSafe2", "fp64"), ("p-BiCGSafe", "fp32"), ("ssBiCGSafe2", "fp32"),
+                           ("p-BiCGSafe-rr", "fp64")]:
+            tm, pr, rs = run(kind, prec, 3, 1)
+            rr = rs[-1]
+            extras["%s_%s" % (kind, prec)] = {
+                "ms_per_solve": tm / 3, "iterations": rr["iterations"], "outer_steps": rr["outer_steps"],
+                "rel_res_true": rr["rel_res_true"], "status": rr["status_name"],
+                "us_per_iter": 1e3 * tm / 3 / max(1, rr["iterations"])}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1:
+            dt, o = cpu_sample(A, b, a.kind, a.cpu_iters)
+            solve_s = dt / a.cpu_iters * iters
+            cpu = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": "%d iterations of the single-threaded FP64 oracle (%s) on the full system in %.1f s, "
+                             "scaled to one solve by the GPU solve's %d iterations" % (a.cpu_iters, a.kind, dt, iters)}
+        line = {"metric": METRIC, "value": world * 1e3 / ms_per_step, "unit": "solves/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "cd3d_%d: 3D -Lap u + 50(u_x+u_y+u_z), %d^3, 7-point upwind, n=%d, nnz=%d, "
+                                       "b=A*1, x0=0" % (a.size, a.size, n, nnz),
+                           "kind": a.kind, "precision": "fp64", "layout": a.layout, "tol": 1e-10,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "no flush: matrix (183 MB) and vectors (16 x 16.8 MB) exceed the 129 MB L2"},
+                "iterations": iters, "outer_steps": outer, "converged_all_steps": ok,
+                "rel_res_true": r0["rel_res_true"], "kernel_ms": kernel_ms,
+                "us_per_iter": 1e3 * kernel_ms / max(1, iters),
+                "gb_per_s_per_iter": achieved_gbs,
+                "roofline": roofline,
+                "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
+                        "d2h_bytes_per_step": n * 8 + 16 * 8},
+                "gpu_launches": a.steps,
+                "clocks": clocks,
+                "cpu_baseline": cpu,
+                "side_by_side": extras}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,281 @@
+"""Thin Python binding of libbcs.so (include/bcs.h).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  Device vectors are passed as torch CUDA tensors (their data_ptr())
+or raw integer device pointers; host arrays as numpy arrays.  Import fails
+loudly when the compiled library is missing: there is no CPU fallback.
+
+Names follow the C ABI: csr_upload, matrix_info, matrix_export, spmv,
+solver_create, solve, solve_host, get_history, get_scalars, solve_batched,
+status_string.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbcs.so")
+
+SSBICGSAFE2, P_BICGSAFE, P_BICGSAFE_RR = 0, 1, 2
+KINDS = {"ssBiCGSafe2": SSBICGSAFE2, "p-BiCGSafe": P_BICGSAFE, "p-BiCGSafe-rr": P_BICGSAFE_RR}
+FP64, FP32_REFINE, BF16MAT_REFINE = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32_REFINE, "bf16": BF16MAT_REFINE}
+LAYOUT_CSR, LAYOUT_SELL = 1, 2
+STORE_F64, STORE_F32, STORE_BF16 = 1, 2, 4
+OK, NOT_CONVERGED, ERR_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NONFINITE, ERR_OOM = 0, 1, -1, -2, -3, -4, -5, -6
+
+EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv",
+            "bcs_matrix_free", "bcs_solver_create", "bcs_solve", "bcs_solve_host", "bcs_get_history",
+            "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_status_string"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rr_m", ctypes.c_int), ("rr_M", ctypes.c_int), ("precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("history_len", ctypes.c_int),
+                ("layout", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("max_ctas", ctypes.c_int), ("spin_budget_ms", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_steps", ctypes.c_int),
+                ("rr_steps", ctypes.c_int), ("fallbacks", ctypes.c_int), ("rel_res_recursive", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("r0_norm", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = status_string(self.status)
+        return d
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libbcs.so is not built (%s); run __graft_entry__.build() or "
+                          "python paper_2108_10591_gb300/build.py" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.bcs_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.bcs_options_default.restype = None
+    L.bcs_csr_upload.argtypes = [I64, I64, P, P, P, I, I, I, I, P, ctypes.POINTER(P)]
+    L.bcs_matrix_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                  ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.bcs_matrix_export.argtypes = [P] * 10
+    L.bcs_spmv.argtypes = [P, I, I, P, P, I, I, P]
+    L.bcs_matrix_free.argtypes = [P]
+    L.bcs_matrix_free.restype = None
+    L.bcs_solver_create.argtypes = [P, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
+    L.bcs_solve.argtypes = [P, P, P, ctypes.POINTER(Result), P]
+    L.bcs_solve_host.argtypes = [P, P, P, ctypes.POINTER(Result), P]
+    L.bcs_get_history.argtypes = [P, P, I, ctypes.POINTER(I)]
+    L.bcs_get_scalars.argtypes = [P, P, I, ctypes.POINTER(I)]
+    L.bcs_solver_destroy.argtypes = [P]
+    L.bcs_solver_destroy.restype = None
+    L.bcs_solve_batched.argtypes = [I, P, I, D, I, ctypes.POINTER(Options), P, P, P, P]
+    L.bcs_status_string.argtypes = [I]
+    L.bcs_status_string.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        getattr(L, name)
+    return L
+
+
+lib = _load()
+
+
+class BcsError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, status_string(code), code))
+        self.code = code
+
+
+def status_string(code):
+    return lib.bcs_status_string(int(code)).decode()
+
+
+def _check(code, what):
+    if code < 0:
+        raise BcsError(code, what)
+    return code
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or an int)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def options(**kw):
+    o = Options()
+    lib.bcs_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "layout" and isinstance(v, str):
+            v = {"csr": LAYOUT_CSR, "sell": LAYOUT_SELL}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Matrix:
+    """Device matrix handle (bcs_matrix)."""
+
+    def __init__(self, handle, n, nnz):
+        self.handle, self.n, self.nnz = handle, n, nnz
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.bcs_matrix_free(self.handle)
+            self.handle = None
+
+    def info(self):
+        return matrix_info(self)
+
+
+def csr_upload(A, layouts=LAYOUT_CSR, sell_C=32, sell_sigma=256, stores=STORE_F64, stream=None):
+    """bcs_csr_upload. A: object with n, rowptr (int64), col (int32), val (float64) host arrays."""
+    rp, ci, va = _np(A.rowptr, np.int64), _np(A.col, np.int32), _np(A.val, np.float64)
+    h = ctypes.c_void_p()
+    _check(lib.bcs_csr_upload(int(A.n), int(rp[-1]), rp.ctypes.data, ci.ctypes.data if len(ci) else None,
+                              va.ctypes.data if len(va) else None, layouts, sell_C, sell_sigma, stores,
+                              _stream(stream), ctypes.byref(h)), "bcs_csr_upload")
+    return Matrix(h.value, int(A.n), int(rp[-1]))
+
+
+def matrix_info(M):
+    n, nnz, pad = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lay, sto = ctypes.c_int(), ctypes.c_int()
+    _check(lib.bcs_matrix_info(M.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(pad), ctypes.byref(lay),
+                               ctypes.byref(sto)), "bcs_matrix_info")
+    return dict(n=n.value, nnz=nnz.value, sell_padded=pad.value, layouts=lay.value, stores=sto.value)
+
+
+def matrix_export(M, csr=True, f32=False, bf16=False, sell=False):
+    """bcs_matrix_export into fresh numpy arrays."""
+    info = matrix_info(M)
+    n, nnz, pad = info["n"], info["nnz"], info["sell_padded"]
+    out = {}
+    args = [None] * 9
+    if csr:
+        out["rowptr"] = np.zeros(n + 1, np.int32)
+        out["col"] = np.zeros(max(nnz, 1), np.int32)
+        out["val64"] = np.zeros(max(nnz, 1), np.float64)
+        args[0], args[1], args[2] = out["rowptr"].ctypes.data, out["col"].ctypes.data, out["val64"].ctypes.data
+    if f32:
+        out["val32"] = np.zeros(max(nnz, 1), np.float32)
+        args[3] = out["val32"].ctypes.data
+    if bf16:
+        out["valbf16"] = np.zeros(max(nnz, 1), np.uint16)
+        args[4] = out["valbf16"].ctypes.data
+    if sell:
+        ns = (n + 31) // 32
+        out["perm"] = np.zeros(max(n, 1), np.int32)
+        out["slice_ptr"] = np.zeros(ns + 1, np.int64)
+        out["scol"] = np.zeros(max(pad, 1), np.int32)
+        out["sval64"] = np.zeros(max(pad, 1), np.float64)
+        args[5], args[6] = out["perm"].ctypes.data, out["slice_ptr"].ctypes.data
+        args[7], args[8] = out["scol"].ctypes.data, out["sval64"].ctypes.data
+    _check(lib.bcs_matrix_export(M.handle, *args), "bcs_matrix_export")
+    for k in ["col", "val64", "val32", "valbf16"]:
+        if k in out:
+            out[k] = out[k][:nnz]
+    if sell:
+        out["perm"] = out["perm"][:n]
+        out["scol"], out["sval64"] = out["scol"][:pad], out["sval64"][:pad]
+    return out
+
+
+def spmv(M, x, y, layout=LAYOUT_CSR, store=STORE_F64, threads_per_row=0, stream=None):
+    """bcs_spmv: y = A x on the device (x, y torch CUDA tensors, float64 or float32)."""
+    import torch
+    f32 = x.dtype == torch.float32
+    _check(lib.bcs_spmv(M.handle, layout, store, _ptr(x), _ptr(y), int(f32), threads_per_row, _stream(stream)),
+           "bcs_spmv")
+    return y
+
+
+class Solver:
+    """Solver handle (bcs_solver)."""
+
+    def __init__(self, M, kind, tol, maxit, opts):
+        self.M = M  # keeps the matrix alive
+        self.opts = opts
+        self.handle = None
+        h = ctypes.c_void_p()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(lib.bcs_solver_create(M.handle, k, float(tol), int(maxit), ctypes.byref(opts), ctypes.byref(h)),
+               "bcs_solver_create")
+        self.handle = h.value
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.bcs_solver_destroy(self.handle)
+            self.handle = None
+
+
+def solver_create(M, kind="p-BiCGSafe", tol=1e-10, maxit=10000, **kw):
+    return Solver(M, kind, tol, maxit, options(**kw))
+
+
+def solve(S, b, x, stream=None):
+    """bcs_solve with device vectors b, x (x holds x_0 on entry). Returns the result as a dict."""
+    r = Result()
+    code = lib.bcs_solve(S.handle, _ptr(b), _ptr(x), ctypes.byref(r), _stream(stream))
+    if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
+        raise BcsError(code, "bcs_solve")
+    return r.as_dict()
+
+
+def solve_host(S, b, x, stream=None):
+    """bcs_solve_host with numpy float64 b and x (x updated in place)."""
+    assert x.dtype == np.float64 and x.flags.c_contiguous
+    bb = _np(b, np.float64)
+    r = Result()
+    code = lib.bcs_solve_host(S.handle, bb.ctypes.data, x.ctypes.data, ctypes.byref(r), _stream(stream))
+    if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
+        raise BcsError(code, "bcs_solve_host")
+    return r.as_dict()
+
+
+def get_history(S):
+    ln = ctypes.c_int()
+    _check(lib.bcs_get_history(S.handle, None, 0, ctypes.byref(ln)), "bcs_get_history")
+    out = np.zeros(max(ln.value, 1))
+    _check(lib.bcs_get_history(S.handle, out.ctypes.data, ln.value, ctypes.byref(ln)), "bcs_get_history")
+    return out[:ln.value]
+
+
+def get_scalars(S):
+    ln = ctypes.c_int()
+    _check(lib.bcs_get_scalars(S.handle, None, 0, ctypes.byref(ln)), "bcs_get_scalars")
+    out = np.zeros(4 * max(ln.value, 1))
+    _check(lib.bcs_get_scalars(S.handle, out.ctypes.data, ln.value, ctypes.byref(ln)), "bcs_get_scalars")
+    return out[:4 * ln.value].reshape(-1, 4)
+
+
+def solve_batched(Ms, bs, xs, kind="p-BiCGSafe", tol=1e-10, maxit=10000, stream=None, **kw):
+    """bcs_solve_batched: lists of matrices and device vectors. Returns (worst status, list of result dicts)."""
+    n = len(Ms)
+    opts = options(**kw)
+    H = (ctypes.c_void_p * n)(*[m.handle for m in Ms])
+    B = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    R = (Result * n)()
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    code = lib.bcs_solve_batched(n, ctypes.cast(H, ctypes.c_void_p), k, float(tol), int(maxit), ctypes.byref(opts),
+                                 ctypes.cast(B, ctypes.c_void_p), ctypes.cast(X, ctypes.c_void_p),
+                                 ctypes.cast(R, ctypes.c_void_p), _stream(stream))
+    if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
+        raise BcsError(code, "bcs_solve_batched")
+    return code, [R[i].as_dict() for i in range(n)]

@@ -1,0 +1,183 @@
+// Device building blocks: memory-ordering primitives, the bounded grid
+// barrier, deterministic block reductions, and the 32-row-tile SpMV used by
+// every solver phase ("MV" in Section 3 / Table 1).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace bcs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- memory ordering -------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch.  A monotonic
+// arrival counter: barrier k completes when the counter reaches k*gridDim.
+// Arrival is a release reduction, the wait an acquire load, so every write
+// made before the barrier by any CTA is visible after it.  The wait is
+// bounded: past `budget` cycles (or when another CTA has already failed) the
+// CTA records BCS_ERR_TIMEOUT and the call returns false; callers then leave
+// the kernel, so a missing CTA can never hang the GPU.
+struct GridBarrier {
+    unsigned* count;
+    int* err;
+    unsigned nblocks;
+    unsigned epoch;
+    long long budget;
+
+    __device__ bool sync(volatile int* s_flag) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            epoch += 1;
+            const unsigned target = epoch * nblocks;
+            red_release_gpu_add(count, 1u);
+            int ok = 1;
+            const long long t0 = clock64();
+            while ((int)(ld_acquire_gpu(count) - target) < 0) {
+                if (ld_relaxed_int(err) != 0) { ok = 0; break; }
+                if (clock64() - t0 > budget) {
+                    atomicCAS(err, 0, (int)BCS_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            *s_flag = ok;
+        }
+        __syncthreads();
+        return *s_flag != 0;
+    }
+};
+
+// ---- reductions --------------------------------------------------------------
+
+// Butterfly sum over the warp: every lane ends with the bitwise-same value
+// (each step adds two identical operand pairs in commuted order).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+// Deterministic block sum of K values per thread.  Result in out[0..K) (shared
+// memory, visible to all threads after return).  scratch: kWarps*K doubles.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) scratch[warp * K + k] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < kWarps ? scratch[lane * K + k] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) out[k] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// ---- value types ---------------------------------------------------------------
+
+__device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
+// BF16 bit pattern -> float (exact: BF16 is the top half of an FP32).
+__device__ __forceinline__ float ldv(const uint16_t* p) {
+    return __uint_as_float(((unsigned)__ldg((const unsigned short*)p)) << 16);
+}
+template <class MT> struct VecOf { typedef float type; };
+template <> struct VecOf<double> { typedef double type; };
+
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// ---- SpMV on a tile of 32 consecutive rows (lane k -> row row0+k) -----------------
+
+// CSR with T lanes per row.  T == 1: each lane sums its row sequentially in
+// storage order with fma (the same order as a plain CSR loop).  T > 1: the
+// T lanes of a group take strided entries of one row, then combine with a
+// butterfly; 32/T rows per pass, results transposed back through shared
+// memory so that lane k holds row row0+k.  Rows >= n yield 0.
+template <class VT, class MT, int T>
+__device__ __forceinline__ VT csr_tile(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                       const MT* __restrict__ val, const VT* x, int64_t row0, int64_t n,
+                                       VT* s_buf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = row0 + lane;
+    int rp0 = 0, rp1 = 0;
+    if (row < n) {
+        rp0 = __ldg(rowptr + row);
+        rp1 = __ldg(rowptr + row + 1);
+    }
+    if constexpr (T == 1) {
+        VT acc = VT(0);
+#pragma unroll 4
+        for (int k = rp0; k < rp1; ++k) acc = vfma((VT)ldv(val + k), x[__ldg(col + k)], acc);
+        return acc;
+    } else {
+        constexpr int G = 32 / T;
+        const int sub = lane % T, grp = lane / T;
+#pragma unroll 1
+        for (int pass = 0; pass < T; ++pass) {
+            const int r = pass * G + grp;
+            const int b = __shfl_sync(kFull, rp0, r);
+            const int e = __shfl_sync(kFull, rp1, r);
+            VT acc = VT(0);
+#pragma unroll 2
+            for (int k = b + sub; k < e; k += T) acc = vfma((VT)ldv(val + k), x[__ldg(col + k)], acc);
+#pragma unroll
+            for (int off = T / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+            if (sub == 0) s_buf[r] = acc;
+        }
+        __syncwarp();
+        const VT v = s_buf[lane];
+        __syncwarp();
+        return v;
+    }
+}
+
+// SELL-C-sigma with C = 32: tile == slice, lane == row of the slice.  The
+// slice is column-major, so each step reads 32 consecutive values and column
+// indices (fully coalesced); each lane sums its row in storage order with fma.
+// Padding (value 0, a valid column) leaves the sum unchanged.
+template <class VT, class MT>
+__device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ scol,
+                                        const MT* __restrict__ sval, const VT* x, int64_t slice) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = __ldg(slice_ptr + slice), e = __ldg(slice_ptr + slice + 1);
+    VT acc = VT(0);
+#pragma unroll 4
+    for (int64_t k = b + lane; k < e; k += 32) acc = vfma((VT)ldv(sval + k), x[__ldg(scol + k)], acc);
+    return acc;
+}
+
+template <class VT, class MT, int LAYOUT, int T>
+__device__ __forceinline__ VT tile_spmv(const KParams& P, const MT* val, const VT* x, int64_t tile, VT* s_buf) {
+    if constexpr (LAYOUT == LAY_SELL) {
+        return sell_tile<VT, MT>(P.slice_ptr, P.col, val, x, tile);
+    } else {
+        return csr_tile<VT, MT, T>(P.rowptr, P.col, val, x, tile * 32, P.n, s_buf);
+    }
+}
+
+}  // namespace bcs

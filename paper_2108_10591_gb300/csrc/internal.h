@@ -1,0 +1,110 @@
+// Internal declarations shared by the translation units of libbcs.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bcs.h"
+
+namespace bcs {
+
+// Slots of the per-CTA inner-product partials (Alg. 3/4: a..h and r; plus the
+// FP64 true-residual norm of the outer step).
+enum Slot { SA = 0, SB, SC, SD, SE, SF, SG, SH, SR, ST, NSLOT_USED, NSLOT = 16 };
+
+// Krylov vectors of one solve (VT = double in FP64 mode, float in the
+// refinement modes).  s and s2 alternate between iterations.
+enum Vec { V_R = 0, V_RS, V_S, V_S2, V_Y, V_T, V_P, V_U, V_Z, V_W, V_L, V_G, V_O, V_BIN, V_D, NVEC };
+
+// Result block written by CTA 0 at the end of a solve (device memory).
+enum Out { O_STATUS = 0, O_ITERS, O_OUTER, O_RR, O_FALLBACK, O_RECREL, O_TRUEREL, O_R0, O_HISTLEN, NOUT = 16 };
+
+enum Layout { LAY_CSR = 0, LAY_SELL = 1 };
+enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+
+constexpr int kBlock = 256;            // threads per CTA of the solver kernels
+constexpr int kWarps = kBlock / 32;
+
+struct KParams {
+    int64_t n;
+    int64_t ntiles;         // 32-row tiles
+    int kind, maxit, rr_m, rr_M, max_outer, mixed, hist_cap;
+    double tol, inner_tol;
+    long long spin_budget;  // clock64 cycles per barrier wait
+    // matrix: CSR (rowptr, col, val) or SELL (slice_ptr, col=scol, val=sval, perm)
+    const int32_t* rowptr;
+    const int32_t* col;
+    const void* val;        // inner-solve value type (MT)
+    const double* val64;    // FP64 values (outer residual)
+    const int32_t* perm;    // SELL: original row of permuted position; nullptr for CSR
+    const int64_t* slice_ptr;
+    // caller vectors (original order)
+    const double* b;
+    double* x;
+    // FP64 working vectors in the solve's row order (== b, x for CSR)
+    double* x64;
+    const double* b64;
+    double* b64w;           // SELL: writable permuted copy of b
+    void* vec[NVEC];
+    double* partials;       // [2][gridDim.x][NSLOT]
+    unsigned* bar;          // barrier counter, zero at launch
+    int* err;               // error flag, zero at launch
+    double* hist;           // [hist_cap]
+    double* scal;           // [4*hist_cap]
+    double* out;            // [NOUT]
+};
+
+// solver kernel launchers (solver_*.cu); return a cudaError_t as int
+int launch_solver(const KParams& P, int vt_f32, int valtype, int layout, int tpr, int grid,
+                  cudaStream_t st, int* max_grid_out);
+int solver_max_grid(int vt_f32, int valtype, int layout, int tpr, int* grid);
+
+}  // namespace bcs
+
+struct bcs_matrix_s {
+    int64_t n = 0, nnz = 0;
+    int layouts = 0, stores = 0;
+    int device = 0;
+    // CSR
+    int32_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val64 = nullptr;
+    float* val32 = nullptr;
+    uint16_t* valbf16 = nullptr;
+    // SELL-C-sigma
+    int sell_C = 32, sell_sigma = 0;
+    int64_t nslices = 0, padded = 0;
+    int32_t* perm = nullptr;
+    int64_t* slice_ptr = nullptr;
+    int32_t* scol = nullptr;
+    double* sval64 = nullptr;
+    float* sval32 = nullptr;
+    uint16_t* svalbf16 = nullptr;
+    double* scratch = nullptr;   // 2n doubles: permuted x and y of bcs_spmv on SELL
+    // row-length statistics (threads-per-row choice)
+    double avg_row = 0;
+    int max_row = 0;
+    int tuned_tpr = 0;
+};
+
+struct bcs_solver_s {
+    bcs_matrix A = nullptr;
+    int kind = 0, maxit = 0;
+    double tol = 0;
+    bcs_options opt;
+    int vt_f32 = 0, valtype = 0, layout = 0, tpr = 1;
+    int grid = 0;
+    size_t vbytes = 0;
+    void* vecmem = nullptr;       // NVEC vectors
+    double* x64w = nullptr;       // SELL: permuted x (FP64)
+    double* b64w = nullptr;       // SELL: permuted b (FP64)
+    double* partials = nullptr;
+    unsigned* bar = nullptr;      // [1] counter, [2] error flag as int (same allocation)
+    double* hist = nullptr;
+    double* scal = nullptr;
+    double* out = nullptr;
+    double* host_out = nullptr;   // pinned copy of out
+    double* xb_dev = nullptr;     // bcs_solve_host staging (2n doubles), allocated on first use
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int hist_len = 0;
+    int last_iters = 0;
+};

@@ -1,0 +1,626 @@
+// The persistent solver kernel: one cooperative launch runs a whole solve
+// (set-up, every iteration of Algorithm 3, 4 or 5, the FP64 true-residual
+// checks and, in the refinement modes, the outer FP64 refinement loop).
+//
+// Mapping: warps own fixed 32-row tiles (tile t -> warp t mod #warps), lane k
+// of a tile owns row 32t+k in every phase, so all vector updates are
+// row-local and coalesced.  Inner products accumulate per thread in FP64,
+// are summed per CTA by a fixed butterfly tree and written as per-CTA
+// partials; after a grid barrier every CTA sums all partials in the same
+// order, so the scalars are bitwise identical in every CTA and no CTA ever
+// has to broadcast them.
+//
+// p-BiCGSafe (Alg. 4) per iteration i, two grid barriers:
+//   phase A  load the partials of iteration i (issued first), compute A s_i
+//            for the warp's first tile while those loads are in flight
+//            (the overlap of the inner-product reduction with MV, Section 3),
+//            finish the reduction -> beta, alpha, zeta, eta, stop test;
+//            then for every tile: A s_i and the fused recurrences for
+//            p, o, u, q, w, t, z, y_{i+1}, x_{i+1}, r_{i+1}, the partial
+//            g' = zeta As + eta g and s' = s - alpha q; partials of
+//            (y,y) (y,r) (r*,r) (r*,t) (r,r).                    -- barrier
+//   phase C  A w_i and l = q - Aw, g_{i+1} = g' - alpha Aw, s_{i+1} = s' - g_{i+1};
+//            partials of (s,s) (s,y) (s,r) (r*,s).                -- barrier
+// ssBiCGSafe2 (Alg. 3), three barriers: A: s = A r + partials of s; B: the
+// reduction (not overlapped) -> scalars, p, o, u; C: w = A u, t, z, y, x, r.
+// p-BiCGSafe-rr (Alg. 5): on i mod m = 0, 0 < i < M the iteration instead
+// runs p,o,u | w = A u, t, z, y, x | r = b - A x, l = A t, g = A y | s = A r.
+//
+// Every multiply-add the paper writes as "a + b*c" is one fma with the
+// operands in the order of the CPU reference formulation, so that with one
+// lane per CSR row (or SELL) the only rounding differences from a plain
+// sequential FP64 implementation are in the inner products.
+#pragma once
+#include <math.h>
+
+#include "device.cuh"
+
+namespace bcs {
+
+// A set of CTAs that solve one system together: the whole cooperative grid
+// (one large system) or one thread-block cluster (batched solves).
+struct GridGroup {
+    GridBarrier gb;
+    int rank, size;
+    __device__ bool sync(volatile int* flag) { return gb.sync(flag); }
+};
+struct ClusterGroup {
+    int rank, size;
+    // barrier.cluster with release/acquire semantics: every write of the
+    // cluster's threads before the barrier is visible after it.  All CTAs of
+    // a cluster are co-scheduled, so the wait always ends.
+    __device__ bool sync(volatile int*) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    }
+};
+
+template <class VT, class MT, int LAYOUT, int T, class Group>
+__device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
+    __shared__ double s_red[kWarps * 10];
+    __shared__ double s_sum[10];
+    __shared__ double s_tmp[10];
+    __shared__ double s_sc[4];
+    __shared__ int s_ctl[2];
+    __shared__ int s_flag;
+    __shared__ VT s_buf[kWarps][32];
+    __shared__ double s_buf64[kWarps][32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gwarp = (int64_t)grp.rank * kWarps + warp;
+    const int64_t nwarps = (int64_t)grp.size * kWarps;
+    const int64_t n = P.n, ntiles = P.ntiles;
+    const int nblk = grp.size;
+    const int rank = grp.rank;
+    const int kind = P.kind;
+    const bool mixed = P.mixed != 0;
+
+    VT* const R = (VT*)P.vec[V_R];
+    VT* const RS = (VT*)P.vec[V_RS];
+    VT* const Y = (VT*)P.vec[V_Y];
+    VT* const Tv = (VT*)P.vec[V_T];
+    VT* const Pv = (VT*)P.vec[V_P];
+    VT* const U = (VT*)P.vec[V_U];
+    VT* const Z = (VT*)P.vec[V_Z];
+    VT* const W = (VT*)P.vec[V_W];
+    VT* const L = (VT*)P.vec[V_L];
+    VT* const G = (VT*)P.vec[V_G];
+    VT* const O = (VT*)P.vec[V_O];
+    VT* const BinW = (VT*)P.vec[V_BIN];
+    VT* sCur = (VT*)P.vec[V_S];
+    VT* sNxt = (VT*)P.vec[V_S2];
+    // The inner system A x_in = b_in: (x64, b64) in FP64 mode, (d, r_outer) in refinement mode.
+    VT* const X = mixed ? (VT*)P.vec[V_D] : (VT*)(void*)P.x64;
+    const VT* const Bin = mixed ? (const VT*)BinW : (const VT*)(const void*)P.b64;
+    const MT* const val = (const MT*)P.val;
+    VT* const sbuf = s_buf[warp];
+    double* const sbuf64 = s_buf64[warp];
+
+    auto spmv = [&](const VT* xv, int64_t tile) -> VT {
+        return tile_spmv<VT, MT, LAYOUT, T>(P, val, xv, tile, sbuf);
+    };
+    auto spmv64 = [&](const double* xv, int64_t tile) -> double {
+        return tile_spmv<double, double, LAYOUT, T>(P, P.val64, xv, tile, sbuf64);
+    };
+    auto pslot = [&](int buf, int c, int k) -> double* {
+        return P.partials + ((size_t)buf * nblk + c) * NSLOT + k;
+    };
+    auto zero10 = [](double (&v)[10]) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) v[k] = 0.0;
+    };
+    // Sum the CTA's per-thread partials and store the slots in `mask`.
+    auto flush = [&](int buf, double (&v)[10], unsigned mask) {
+        block_sum<10>(v, s_red, s_tmp);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 10; ++k)
+                if ((mask >> k) & 1u) *pslot(buf, rank, k) = s_tmp[k];
+        }
+    };
+    auto load_partials = [&](int buf, double (&v)[10]) {
+        zero10(v);
+        for (int c = threadIdx.x; c < nblk; c += kBlock) {
+            const double* src = pslot(buf, c, 0);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) v[k] += src[k];
+        }
+    };
+    auto dacc = [](double& acc, VT a, VT b) { acc = fma((double)a, (double)b, acc); };
+
+    // ---- SELL: the solve runs in the permuted row order ----
+    if (P.perm != nullptr) {
+        for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+            const int64_t row = tile * 32 + lane;
+            if (row < n) {
+                const int32_t src = __ldg(P.perm + row);
+                P.x64[row] = P.x[src];
+                P.b64w[row] = P.b[src];
+            }
+        }
+        if (!grp.sync(&s_flag)) return;
+    }
+
+    int status = BCS_NOT_CONVERGED, inner_status = BCS_OK;
+    int total = 0, evals = 0, runs = 0, hist_len = 0, rr_steps = 0, fallbacks = 0;
+    double r0n = 0.0, thresh = 0.0, r0ref = 1.0, rtrue = 0.0, last_rec = 0.0;
+    double alpha_p = 0.0, zeta_p = 0.0, f_p = 0.0;  // thread 0 of each CTA
+
+    for (;;) {
+        // ---------------- true residual r = b - A x (FP64) and (re)initialisation ----------
+        {
+            double pv[10];
+            zero10(pv);
+            for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const double ax = spmv64(P.x64, tile);
+                const int64_t row = tile * 32 + lane;
+                if (row < n) {
+                    const double r64 = P.b64[row] - ax;
+                    pv[ST] = fma(r64, r64, pv[ST]);
+                    const VT rv = (VT)r64;
+                    R[row] = rv;
+                    RS[row] = rv;
+                    if (mixed) {
+                        BinW[row] = rv;
+                        X[row] = VT(0);
+                    }
+                    Y[row] = VT(0); Tv[row] = VT(0); Pv[row] = VT(0); U[row] = VT(0);
+                    Z[row] = VT(0); W[row] = VT(0); L[row] = VT(0); G[row] = VT(0);
+                    dacc(pv[SF], rv, rv);
+                }
+            }
+            pv[SR] = pv[SF];
+            flush(0, pv, (1u << ST) | (1u << SF) | (1u << SR) | (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH));
+            if (!grp.sync(&s_flag)) return;
+            load_partials(0, pv);
+            block_sum<10>(pv, s_red, s_sum);
+            const double rt2 = s_sum[ST];
+            rtrue = sqrt(rt2);
+            if (evals == 0) {
+                r0n = rtrue;
+                thresh = P.tol * r0n;
+                r0ref = r0n > 0.0 ? r0n : 1.0;
+            }
+            ++evals;
+            if (inner_status != BCS_OK) { status = inner_status; break; }
+            if (rtrue <= thresh) { status = BCS_OK; break; }
+            if (runs >= P.max_outer) { status = BCS_NOT_CONVERGED; break; }
+        }
+        ++runs;
+        const double thr_in = mixed ? P.inner_tol * rtrue : thresh;
+        const int budget = P.maxit - total;
+
+        // ---------------- pipelined set-up: s_0 = A r_0 and the i = 0 products --------------
+        if (kind != BCS_SSBICGSAFE2) {
+            double pv[10];
+            zero10(pv);
+            for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const VT sv = spmv(R, tile);
+                const int64_t row = tile * 32 + lane;
+                if (row < n) {
+                    sCur[row] = sv;
+                    const VT rv = R[row], rsv = RS[row];
+                    dacc(pv[SA], sv, sv);
+                    dacc(pv[SD], sv, rv);
+                    dacc(pv[SG], rsv, sv);
+                }
+            }
+            flush(0, pv, (1u << SA) | (1u << SD) | (1u << SG));
+            if (!grp.sync(&s_flag)) return;
+        }
+
+        // ---------------- iterations ----------------------------------------------------------
+        int i = 0;
+        for (;; ++i) {
+            const int cur = i & 1, nxt = cur ^ 1;
+            const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
+            double pv[10];
+            VT as_first = VT(0);
+            if (kind == BCS_SSBICGSAFE2) {
+                // phase A: s_i = A r_i and the products involving s_i
+                zero10(pv);
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT sv = spmv(R, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        sCur[row] = sv;
+                        const VT yv = Y[row], rv = R[row], rsv = RS[row];
+                        dacc(pv[SA], sv, sv);
+                        dacc(pv[SC], sv, yv);
+                        dacc(pv[SD], sv, rv);
+                        dacc(pv[SG], rsv, sv);
+                    }
+                }
+                flush(cur, pv, (1u << SA) | (1u << SC) | (1u << SD) | (1u << SG));
+                if (!grp.sync(&s_flag)) return;
+                load_partials(cur, pv);
+            } else {
+                // phase A: the reduction of iteration i overlaps A s_i of the first tile
+                load_partials(cur, pv);
+                if (!rr_step && gwarp < ntiles) as_first = spmv(sCur, gwarp);
+            }
+            block_sum<10>(pv, s_red, s_sum);
+
+            // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
+            if (threadIdx.x == 0) {
+                const double a = s_sum[SA], bb = s_sum[SB], c = s_sum[SC], d = s_sum[SD], e = s_sum[SE];
+                const double f = s_sum[SF], g = s_sum[SG], h = s_sum[SH], rr = s_sum[SR];
+                double alpha, beta, zeta, eta;
+                bool brk;
+                if (i == 0) {
+                    beta = 0.0;
+                    alpha = f / g;
+                    zeta = d / a;
+                    eta = 0.0;
+                    brk = (g == 0.0 || a == 0.0);
+                } else {
+                    beta = (alpha_p * f) / (zeta_p * f_p);
+                    alpha = f / (g + beta * h);
+                    const double den = a * bb - c * c;
+                    if (den == 0.0 || !isfinite(den)) {
+                        zeta = d / a;
+                        eta = 0.0;
+                        ++fallbacks;
+                    } else {
+                        zeta = (bb * d - c * e) / den;
+                        eta = (a * e - c * d) / den;
+                    }
+                    brk = (zeta_p * f_p == 0.0 || g + beta * h == 0.0 || a == 0.0);
+                }
+                const double rn = sqrt(rr);
+                const bool conv = rn <= thr_in;
+                int dec = 0, st = BCS_OK;
+                if (brk && !conv) {
+                    dec = 1;
+                    st = BCS_ERR_BREAKDOWN;
+                } else {
+                    if (rank == 0) {
+                        if (hist_len < P.hist_cap) P.hist[hist_len] = rn / r0ref;
+                        if (runs == 1 && i < P.hist_cap) {
+                            P.scal[4 * i + 0] = alpha; P.scal[4 * i + 1] = beta;
+                            P.scal[4 * i + 2] = zeta;  P.scal[4 * i + 3] = eta;
+                        }
+                    }
+                    ++hist_len;
+                    last_rec = rn / r0ref;
+                    if (conv) { dec = 1; st = BCS_OK; }
+                    else if (!isfinite(alpha) || !isfinite(beta) || !isfinite(zeta) || !isfinite(eta) || !isfinite(rr)) {
+                        dec = 1; st = BCS_ERR_NONFINITE;
+                    } else if (i >= budget) { dec = 1; st = BCS_NOT_CONVERGED; }
+                }
+                s_sc[0] = alpha; s_sc[1] = beta; s_sc[2] = zeta; s_sc[3] = eta;
+                s_ctl[0] = dec; s_ctl[1] = st;
+                alpha_p = alpha; zeta_p = zeta; f_p = f;
+            }
+            __syncthreads();
+            if (s_ctl[0]) { inner_status = s_ctl[1]; break; }
+            const VT al = (VT)s_sc[0], be = (VT)s_sc[1], ze = (VT)s_sc[2], et = (VT)s_sc[3];
+
+            if (kind == BCS_SSBICGSAFE2) {
+                // phase B: p_i, o_i, u_i
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT r = R[row], s = sCur[row], t = Tv[row], y = Y[row];
+                        VT p = Pv[row], u = U[row];
+                        p = vfma(be, p - u, r);
+                        const VT o = vfma(be, t, s);
+                        u = vfma(ze, o, et * vfma(be, u, y));
+                        Pv[row] = p; O[row] = o; U[row] = u;
+                    }
+                }
+                if (!grp.sync(&s_flag)) return;
+                // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
+                zero10(pv);
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT w = spmv(U, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT o = O[row], r = R[row], u = U[row], s = sCur[row], y = Y[row], p = Pv[row], rs = RS[row];
+                        VT z = Z[row], x = X[row];
+                        const VT t = o - w;
+                        z = vfma(-al, u, vfma(ze, r, et * z));
+                        const VT yn = vfma(-al, w, vfma(ze, s, et * y));
+                        x = vfma(al, p, x) + z;
+                        const VT rn = vfma(-al, o, r) - yn;
+                        Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x; R[row] = rn;
+                        dacc(pv[SB], yn, yn);
+                        dacc(pv[SE], yn, rn);
+                        dacc(pv[SF], rs, rn);
+                        dacc(pv[SH], rs, t);
+                        dacc(pv[SR], rn, rn);
+                    }
+                }
+                flush(nxt, pv, (1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR));
+                if (!grp.sync(&s_flag)) return;
+            } else if (!rr_step) {
+                // phase A (continued): fused recurrences of Alg. 4
+                zero10(pv);
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT As = (tile == gwarp) ? as_first : spmv(sCur, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT r = R[row], s = sCur[row], rs = RS[row];
+                        VT p = Pv[row], u = U[row], t = Tv[row], l = L[row], y = Y[row], g = G[row];
+                        VT w = W[row], z = Z[row], x = X[row];
+                        p = vfma(be, p - u, r);
+                        const VT o = vfma(be, t, s);
+                        u = vfma(ze, o, et * vfma(be, u, y));
+                        const VT q = vfma(be, l, As);
+                        w = vfma(ze, q, et * vfma(be, w, g));
+                        t = o - w;
+                        z = vfma(-al, u, vfma(ze, r, et * z));
+                        const VT yn = vfma(-al, w, vfma(ze, s, et * y));
+                        x = vfma(al, p, x) + z;
+                        const VT rn = vfma(-al, o, r) - yn;
+                        const VT gp = vfma(ze, As, et * g);
+                        const VT sa = vfma(-al, q, s);
+                        Pv[row] = p; U[row] = u; W[row] = w; Tv[row] = t; Z[row] = z;
+                        Y[row] = yn; X[row] = x; R[row] = rn; L[row] = q; G[row] = gp; sNxt[row] = sa;
+                        dacc(pv[SB], yn, yn);
+                        dacc(pv[SE], yn, rn);
+                        dacc(pv[SF], rs, rn);
+                        dacc(pv[SH], rs, t);
+                        dacc(pv[SR], rn, rn);
+                    }
+                }
+                flush(nxt, pv, (1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR));
+                if (!grp.sync(&s_flag)) return;
+                // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
+                zero10(pv);
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT Aw = spmv(W, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT q = L[row], gp = G[row], sa = sNxt[row];
+                        const VT l = q - Aw;
+                        const VT g = vfma(-al, Aw, gp);
+                        const VT s = sa - g;
+                        L[row] = l; G[row] = g; sNxt[row] = s;
+                        const VT y = Y[row], r = R[row], rs = RS[row];
+                        dacc(pv[SA], s, s);
+                        dacc(pv[SC], s, y);
+                        dacc(pv[SD], s, r);
+                        dacc(pv[SG], rs, s);
+                    }
+                }
+                flush(nxt, pv, (1u << SA) | (1u << SC) | (1u << SD) | (1u << SG));
+                if (!grp.sync(&s_flag)) return;
+                VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
+            } else {
+                // residual replacement iteration (Alg. 5)
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT r = R[row], s = sCur[row], t = Tv[row], y = Y[row];
+                        VT p = Pv[row], u = U[row];
+                        p = vfma(be, p - u, r);
+                        const VT o = vfma(be, t, s);
+                        u = vfma(ze, o, et * vfma(be, u, y));
+                        Pv[row] = p; O[row] = o; U[row] = u;
+                    }
+                }
+                if (!grp.sync(&s_flag)) return;
+                // w_i = A u_i (q_i = A o_i is not used after a replacement); t, z, y_{i+1}, x_{i+1}
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT w = spmv(U, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT o = O[row], r = R[row], u = U[row], s = sCur[row], y = Y[row], p = Pv[row];
+                        VT z = Z[row], x = X[row];
+                        const VT t = o - w;
+                        z = vfma(-al, u, vfma(ze, r, et * z));
+                        const VT yn = vfma(-al, w, vfma(ze, s, et * y));
+                        x = vfma(al, p, x) + z;
+                        W[row] = w; Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x;
+                    }
+                }
+                if (!grp.sync(&s_flag)) return;
+                // r_{i+1} = b - A x_{i+1}; l_i = A t_i; g_{i+1} = A y_{i+1}
+                zero10(pv);
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT ax = spmv(X, tile);
+                    const VT at = spmv(Tv, tile);
+                    const VT ay = spmv(Y, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        const VT rn = Bin[row] - ax;
+                        const VT y = Y[row], t = Tv[row], rs = RS[row];
+                        R[row] = rn; L[row] = at; G[row] = ay;
+                        dacc(pv[SB], y, y);
+                        dacc(pv[SE], y, rn);
+                        dacc(pv[SF], rs, rn);
+                        dacc(pv[SH], rs, t);
+                        dacc(pv[SR], rn, rn);
+                    }
+                }
+                flush(nxt, pv, (1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR));
+                if (!grp.sync(&s_flag)) return;
+                // s_{i+1} = A r_{i+1}
+                zero10(pv);
+                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                    const VT s = spmv(R, tile);
+                    const int64_t row = tile * 32 + lane;
+                    if (row < n) {
+                        sNxt[row] = s;
+                        const VT y = Y[row], r = R[row], rs = RS[row];
+                        dacc(pv[SA], s, s);
+                        dacc(pv[SC], s, y);
+                        dacc(pv[SD], s, r);
+                        dacc(pv[SG], rs, s);
+                    }
+                }
+                flush(nxt, pv, (1u << SA) | (1u << SC) | (1u << SD) | (1u << SG));
+                if (!grp.sync(&s_flag)) return;
+                ++rr_steps;
+                VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
+            }
+        }
+        total += i;
+        // refinement: x += d in FP64 (not after a non-finite inner run)
+        if (mixed && inner_status != BCS_ERR_NONFINITE) {
+            for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const int64_t row = tile * 32 + lane;
+                if (row < n) P.x64[row] += (double)X[row];
+            }
+        }
+        if (!grp.sync(&s_flag)) return;
+    }
+
+    if (rank == 0 && threadIdx.x == 0) {
+        P.out[O_STATUS] = status;
+        P.out[O_ITERS] = total;
+        P.out[O_OUTER] = runs;
+        P.out[O_RR] = rr_steps;
+        P.out[O_FALLBACK] = fallbacks;
+        P.out[O_RECREL] = last_rec;
+        P.out[O_TRUEREL] = rtrue / r0ref;
+        P.out[O_R0] = r0n;
+        P.out[O_HISTLEN] = hist_len;
+    }
+    if (P.perm != nullptr) {
+        for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+            const int64_t row = tile * 32 + lane;
+            if (row < n) P.x[__ldg(P.perm + row)] = P.x64[row];
+        }
+    }
+}
+
+template <class VT, class MT, int LAYOUT, int T>
+__global__ void __launch_bounds__(kBlock) solve_kernel(const __grid_constant__ KParams P) {
+    GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
+    solve_body<VT, MT, LAYOUT, T>(P, grp);
+}
+
+template <class VT, class MT, int LAYOUT, int T>
+int launch_one(const KParams& P, int grid, cudaStream_t st) {
+    void* args[] = {(void*)&P};
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T>, dim3(grid), dim3(kBlock),
+                                            args, 0, st);
+}
+
+template <class VT, class MT, int LAYOUT, int T>
+int max_grid_one(int* grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T>, kBlock, 0);
+    *grid = sms * per;
+    return (int)e;
+}
+
+// Dispatch over layout and lanes-per-row for one (VT, MT) pair.
+template <class VT, class MT>
+int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
+#define BCS_CASE(LAY, TT)                                                              \
+    return P ? launch_one<VT, MT, LAY, TT>(*P, grid, st) : max_grid_one<VT, MT, LAY, TT>(max_grid)
+    if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1); }
+    switch (tpr) {
+        case 1: BCS_CASE(LAY_CSR, 1);
+        case 2: BCS_CASE(LAY_CSR, 2);
+        case 4: BCS_CASE(LAY_CSR, 4);
+        case 8: BCS_CASE(LAY_CSR, 8);
+        case 16: BCS_CASE(LAY_CSR, 16);
+        default: BCS_CASE(LAY_CSR, 32);
+    }
+#undef BCS_CASE
+}
+
+}  // namespace bcs
+
+namespace bcs {
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_id_x() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Batched solves: each thread-block cluster takes systems from a work list
+// (largest first) and solves them one after another with the same body as
+// the single-system kernel; cluster barriers replace the grid barrier.
+// sys[k]: the system's parameters without workspace; the cluster's own
+// vectors (NVEC x max_n) and partials are patched in.
+struct BatchArgs {
+    const KParams* sys;
+    const int* order;
+    int nsys;
+    int* counter;
+    int* slots;
+    char* ws;
+    size_t ws_group_bytes, vec_bytes;
+    double* partials;
+    int csize;
+};
+
+template <class VT, class MT, int T>
+__global__ void __launch_bounds__(kBlock) batched_kernel(const __grid_constant__ BatchArgs B) {
+    __shared__ KParams sP;
+    __shared__ int s_dummy;
+    ClusterGroup grp{(int)cluster_ctarank(), (int)cluster_nctarank()};
+    const int cid = (int)cluster_id_x();
+    for (;;) {
+        if (grp.rank == 0 && threadIdx.x == 0) B.slots[cid] = atomicAdd(B.counter, 1);
+        grp.sync(&s_dummy);
+        const int k = ld_relaxed_int(B.slots + cid);
+        grp.sync(&s_dummy);
+        if (k >= B.nsys) break;
+        if (threadIdx.x == 0) {
+            sP = B.sys[B.order[k]];
+            char* base = B.ws + (size_t)cid * B.ws_group_bytes;
+            for (int v = 0; v < NVEC; ++v) sP.vec[v] = base + (size_t)v * B.vec_bytes;
+            sP.partials = B.partials + (size_t)cid * 2 * B.csize * NSLOT;
+        }
+        __syncthreads();
+        solve_body<VT, MT, LAY_CSR, T>(sP, grp);
+    }
+}
+
+template <class VT, class MT>
+int dispatch_batched(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = B->csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void (*fn)(BatchArgs) = nullptr;
+    switch (tpr) {
+        case 1: fn = batched_kernel<VT, MT, 1>; break;
+        case 4: fn = batched_kernel<VT, MT, 4>; break;
+        case 8: fn = batched_kernel<VT, MT, 8>; break;
+        default: fn = batched_kernel<VT, MT, 32>; break;
+    }
+    cudaError_t e = cudaSuccess;
+    if (B->csize > 8) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return (int)e;
+    if (max_clusters) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cfg.gridDim = dim3(B->csize * sms);
+        int mc = 0;
+        e = cudaOccupancyMaxActiveClusters(&mc, (const void*)fn, &cfg);
+        *max_clusters = mc;
+        return (int)e;
+    }
+    cfg.gridDim = dim3(B->csize * nclusters);
+    return (int)cudaLaunchKernelEx(&cfg, fn, *B);
+}
+
+}  // namespace bcs

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Integer and format work must match bit for bit;
+floating point within the stated tolerances:
+  - SpMV, one lane per row or SELL: bit-exact (same fma order per row);
+    several lanes per row: |dy| <= 2 gamma_len * sum|a_ij x_j| per row, the
+    recursive-summation error bound of either order (gamma_m = m u / (1 - m u));
+  - FP64 residual histories: 1e-8 relative over the first 20 iterations;
+  - final FP64 true residual <= tol, iteration count within +-5% of the oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ["ssBiCGSafe2", "p-BiCGSafe", "p-BiCGSafe-rr"]
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2108_10591_gb300 as bcs
+    return bcs, torch, orc
+
+
+def _abs_row_bound(A, x):
+    """sum_j |a_ij x_j| per row (numpy)."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    out = np.zeros(A.n)
+    np.add.at(out, rows, np.abs(A.val * x[A.col]))
+    return out
+
+
+def _empty_rows_matrix():
+    D = np.zeros((70, 70))
+    rng = np.random.default_rng(4)
+    for i in range(70):
+        if i % 7 == 3:
+            continue  # empty row
+        cols = rng.choice(70, size=rng.integers(1, 9), replace=False)
+        D[i, cols] = rng.standard_normal(len(cols))
+    return W.dense_to_csr(D)
+
+
+MATS = {
+    "cd2d_64": lambda: W.cd2d(64, 20.0),
+    "cd2d_45_ragged": lambda: W.cd2d(45, 7.0),
+    "cd3d27_9": lambda: W.cd3d27(9, 100.0),
+    "powerlaw_20k": lambda: W.powerlaw(n=20000, seed=5),
+    "empty_rows_70": _empty_rows_matrix,
+    "n1": lambda: W.dense_to_csr(np.array([[2.5]])),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+def test_spmv_fp64(env, name):
+    bcs, torch, orc = env
+    A = MATS[name]()
+    M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL, sell_sigma=256)
+    x = np.random.default_rng(1).standard_normal(A.n)
+    want = orc.spmv(A, x)
+    xd = torch.from_numpy(x).cuda()
+    lens = np.diff(A.rowptr)
+    u = 2.0 ** -53
+    bound = 2 * (lens + 1) * u / (1 - (lens + 1) * u) * _abs_row_bound(A, x)
+    for lay, tpr in [(bcs.LAYOUT_SELL, 0), (bcs.LAYOUT_CSR, 1), (bcs.LAYOUT_CSR, 2), (bcs.LAYOUT_CSR, 4),
+                     (bcs.LAYOUT_CSR, 8), (bcs.LAYOUT_CSR, 16), (bcs.LAYOUT_CSR, 32)]:
+        yd = torch.full_like(xd, np.nan)
+        bcs.spmv(M, xd, yd, layout=lay, threads_per_row=tpr)
+        y = yd.cpu().numpy()
+        if lay == bcs.LAYOUT_SELL or tpr == 1:
+            assert np.array_equal(y, want), (lay, tpr)
+        else:
+            assert np.all(np.abs(y - want) <= bound), (lay, tpr)
+
+
+@pytest.mark.parametrize("name", ["cd2d_45_ragged", "powerlaw_20k", "empty_rows_70"])
+def test_spmv_low_precision(env, name):
+    """FP32 / BF16 value copies with FP32 vectors: within the FP32 accumulation bound of the
+    exact product of the stored (rounded) values."""
+    bcs, torch, orc = env
+    A = MATS[name]()
+    M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL, stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    x32 = np.random.default_rng(2).standard_normal(A.n).astype(np.float32)
+    xd = torch.from_numpy(x32).cuda()
+    lens = np.diff(A.rowptr)
+    for store in [bcs.STORE_F32, bcs.STORE_BF16]:
+        if store == bcs.STORE_F32:
+            vals = A.val.astype(np.float32).astype(np.float64)
+        else:
+            bits = orc.to_bf16_bits(A.val)
+            vals = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        Ar = W.CSR(A.n, A.rowptr, A.col, vals)
+        exact = orc.spmv(Ar, x32.astype(np.float64))
+        bound = _abs_row_bound(Ar, x32.astype(np.float64)) * (lens + 1) * 2.0 ** -24
+        for lay, tpr in [(bcs.LAYOUT_SELL, 0), (bcs.LAYOUT_CSR, 1), (bcs.LAYOUT_CSR, 8)]:
+            yd = torch.zeros_like(xd)
+            bcs.spmv(M, xd, yd, layout=lay, store=store, threads_per_row=tpr)
+            y = yd.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(y - exact) <= bound + 1e-30), (store, lay, tpr)
+
+
+@pytest.mark.parametrize("name", ["cd2d_45_ragged", "powerlaw_20k", "empty_rows_70", "cd3d27_9"])
+def test_format_build_bit_exact(env, name):
+    """CSR, FP32/BF16 rounding and SELL-C-sigma built on the device equal the oracle's, bit for bit."""
+    bcs, torch, orc = env
+    A = MATS[name]()
+    for sigma in [32, 256]:
+        M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL, sell_sigma=sigma,
+                           stores=bcs.STORE_F32 | bcs.STORE_BF16)
+        E = bcs.matrix_export(M, csr=True, f32=True, bf16=True, sell=True)
+        assert np.array_equal(E["rowptr"], A.rowptr.astype(np.int32))
+        assert np.array_equal(E["col"], A.col)
+        assert np.array_equal(E["val64"].view(np.uint64), A.val.view(np.uint64))
+        assert np.array_equal(E["val32"].view(np.uint32), A.val.astype(np.float32).view(np.uint32))
+        assert np.array_equal(E["valbf16"], orc.to_bf16_bits(A.val))
+        S = orc.sell_build(A, 32, sigma)
+        assert np.array_equal(E["perm"], S["perm"])
+        assert np.array_equal(E["slice_ptr"], S["slice_ptr"])
+        assert np.array_equal(E["scol"], S["col"])
+        assert np.array_equal(E["sval64"].view(np.uint64), S["val"].view(np.uint64))
+
+
+def test_upload_rejects_invalid_csr(env):
+    bcs, torch, orc = env
+    good = W.cd2d(8, 1.0)
+    bad_cases = []
+    c = W.CSR(good.n, good.rowptr.copy(), good.col.copy(), good.val.copy())
+    c.col[1], c.col[2] = c.col[2], c.col[1]  # unsorted row
+    bad_cases.append(c)
+    c = W.CSR(good.n, good.rowptr.copy(), good.col.copy(), good.val.copy())
+    c.col[5] = good.n  # out of range
+    bad_cases.append(c)
+    c = W.CSR(good.n, good.rowptr.copy(), good.col.copy(), good.val.copy())
+    c.rowptr[3], c.rowptr[4] = c.rowptr[4], c.rowptr[3]  # decreasing rowptr
+    bad_cases.append(c)
+    c = W.CSR(good.n, good.rowptr.copy(), good.col.copy(), good.val.copy())
+    c.col[7] = c.col[6]  # duplicate
+    bad_cases.append(c)
+    for c in bad_cases:
+        with pytest.raises(bcs.BcsError) as ei:
+            bcs.csr_upload(c)
+        assert ei.value.code == bcs.ERR_ARG
+
+
+def _gpu_solve(bcs, torch, A, b, kind, **kw):
+    tol = kw.pop("tol", 1e-10)
+    maxit = kw.pop("maxit", 5000)
+    layouts = bcs.LAYOUT_CSR | bcs.LAYOUT_SELL
+    M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    S = bcs.solver_create(M, kind, tol=tol, maxit=maxit, **kw)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, xd)
+    return res, xd.cpu().numpy(), bcs.get_history(S), bcs.get_scalars(S)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("cfg", [dict(threads_per_row=1), dict(layout="sell"), dict(threads_per_row=4),
+                                 dict(threads_per_row=1, max_ctas=3)])
+def test_solver_parity_cd2d_64(env, kind, cfg):
+    """64x64 convection-diffusion (the small FP64 configuration): histories, scalars,
+    iteration count and true residual against the oracle."""
+    bcs, torch, orc = env
+    A = W.cd2d(64, 20.0)
+    b = W.rhs_ones(A)
+    res, x, h, sc = _gpu_solve(bcs, torch, A, b, kind, rr_m=100, **cfg)
+    ref = orc.solve(A, b, kind=kind, tol=1e-10, maxit=5000, rr_m=100, max_restarts=29)
+    assert res["status"] == 0, res
+    assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
+    assert res["rel_res_true"] <= 1e-10
+    assert abs(res["iterations"] - ref["iterations"]) <= max(1, 0.05 * ref["iterations"]), (res, ref["iterations"])
+    k = 20
+    rel = np.abs(h[:k] - ref["hist"][:k]) / ref["hist"][:k]
+    assert np.max(rel) <= 1e-8, rel
+    assert np.max(np.abs(sc[:k] - ref["scalars"][:k]) / np.abs(ref["scalars"][:k]).clip(1e-300)) <= 1e-6
+    assert np.max(np.abs(x - ref["x"])) <= 1e-7
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_solver_parity_ragged_powerlaw(env, kind):
+    """Irregular rows, n not a multiple of 32, several CTAs."""
+    bcs, torch, orc = env
+    A = W.powerlaw(n=20001, seed=9)
+    b = W.rhs_ones(A)
+    res, x, h, sc = _gpu_solve(bcs, torch, A, b, kind, threads_per_row=1, rr_m=10, max_ctas=16)
+    ref = orc.solve(A, b, kind=kind, tol=1e-10, maxit=5000, rr_m=10, max_restarts=29)
+    assert res["status"] == 0
+    assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
+    assert abs(res["iterations"] - ref["iterations"]) <= max(1, 0.05 * ref["iterations"])
+    k = min(20, len(ref["hist"]))
+    assert np.max(np.abs(h[:k] - ref["hist"][:k]) / ref["hist"][:k]) <= 1e-8
+    assert res["rr_steps"] == ref["rr_steps"] or kind != "p-BiCGSafe-rr"
+
+
+def test_residual_replacement_counts(env):
+    bcs, torch, orc = env
+    A = W.cd2d(40, 30.0)
+    b = W.rhs_ones(A)
+    res, x, h, _ = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe-rr", threads_per_row=1, rr_m=7, rr_M=50)
+    ref = orc.solve(A, b, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=7, rr_M=50, max_restarts=29)
+    assert res["status"] == 0 and res["rr_steps"] == ref["rr_steps"] == 7
+    k = 20
+    assert np.max(np.abs(h[:k] - ref["hist"][:k]) / ref["hist"][:k]) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe"])
+def test_mixed_precision_reaches_fp64_tolerance(env, prec, kind):
+    """FP32/BF16 inner solves + FP64 refinement: FP64 true residual <= 1e-10 and the
+    error against the FP64 oracle's solution within the conditioning bound."""
+    bcs, torch, orc = env
+    A = W.cd2d(64, 20.0)
+    b = W.rhs_ones(A)
+    res, x, _, _ = _gpu_solve(bcs, torch, A, b, kind, precision=prec, threads_per_row=1)
+    ref = orc.solve(A, b, kind=kind, tol=1e-10, maxit=5000, max_restarts=29)
+    assert res["status"] == 0, res
+    tr = orc.true_residual(A, b, x) / np.linalg.norm(b)
+    assert tr <= 1e-10
+    assert np.max(np.abs(x - ref["x"])) <= 1e-7
+    assert res["outer_steps"] >= 2
+
+
+def test_edge_cases(env):
+    bcs, torch, orc = env
+    # b = 0: converged at the first check, x stays x_0 = 0
+    A = W.cd2d(10, 1.0)
+    res, x, h, _ = _gpu_solve(bcs, torch, A, np.zeros(A.n), "p-BiCGSafe")
+    assert res["status"] == 0 and res["iterations"] == 0 and np.all(x == 0)
+    # n = 1
+    A1 = W.dense_to_csr(np.array([[4.0]]))
+    res, x, h, _ = _gpu_solve(bcs, torch, A1, np.array([2.0]), "ssBiCGSafe2")
+    assert res["status"] == 0 and abs(x[0] - 0.5) < 1e-15
+    # maxit reached -> not converged, x finite
+    res, x, h, _ = _gpu_solve(bcs, torch, W.cd2d(64, 20.0), W.rhs_ones(W.cd2d(64, 20.0)), "p-BiCGSafe", maxit=5)
+    assert res["status"] == bcs.NOT_CONVERGED and res["iterations"] == 5 and np.all(np.isfinite(x))
+
+
+def test_determinism(env):
+    """Same inputs, same launch configuration -> bitwise identical results."""
+    bcs, torch, orc = env
+    A = W.powerlaw(n=30000, seed=3)
+    b = W.rhs_ones(A)
+    r1 = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", threads_per_row=8)
+    r2 = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", threads_per_row=8)
+    assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched(env, prec):
+    """Independent systems of uneven size in one launch, each against its own oracle solve."""
+    bcs, torch, orc = env
+    mats, sides, betas = W.batch_cd2d(count=12, seed=7, kmin=8, kmax=40)
+    Ms, bs, xs, refs = [], [], [], []
+    for A in mats:
+        b = W.rhs_ones(A)
+        Ms.append(bcs.csr_upload(A, stores=bcs.STORE_F32))
+        bs.append(torch.from_numpy(b).cuda())
+        xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+        refs.append(orc.solve(A, b, kind="p-BiCGSafe", tol=1e-10, maxit=5000, max_restarts=29))
+    code, res = bcs.solve_batched(Ms, bs, xs, kind="p-BiCGSafe", tol=1e-10, maxit=5000, precision=prec)
+    assert code == 0
+    for A, b, x, r, ref in zip(mats, bs, xs, res, refs):
+        xh = x.cpu().numpy()
+        assert r["status"] == 0
+        assert orc.true_residual(A, b.cpu().numpy(), xh) / np.linalg.norm(b.cpu().numpy()) <= 1e-10
+        if prec == "fp64":
+            assert abs(r["iterations"] - ref["iterations"]) <= max(2, 0.05 * ref["iterations"])
+        assert np.max(np.abs(xh - 1.0)) <= 1e-6

@@ -1,0 +1,80 @@
+"""CPU-only checks of the C ABI library: it loads, exports every entry point
+that include/bcs.h declares, and its host-side argument checks return the
+documented codes without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bcs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2108_10591_gb300 as m
+    return m
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "bcs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bcs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ["bcs_csr_upload", "bcs_solver_create", "bcs_solve", "bcs_solve_batched"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(bcs):
+    lib = ctypes.CDLL(bcs.LIB_PATH)
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+    assert sorted(declared_symbols()) == sorted(bcs.EXPORTED)
+
+
+def test_status_strings(bcs):
+    for code in [0, 1, -1, -2, -3, -4, -5, -6]:
+        assert bcs.status_string(code) not in ("", "unknown status")
+    assert bcs.status_string(12345) == "unknown status"
+
+
+def test_options_default(bcs):
+    o = bcs.options()
+    assert o.rr_m == 100 and o.precision == bcs.FP64 and o.max_outer == 30 and o.inner_tol == 1e-3
+    assert o.layout == bcs.LAYOUT_CSR and o.spin_budget_ms > 0
+
+
+def test_argument_checks_without_gpu(bcs):
+    lib = bcs.lib
+    h = ctypes.c_void_p()
+    rp = np.array([0, 1], dtype=np.int64)
+    ci = np.array([0], dtype=np.int32)
+    va = np.array([1.0])
+    # negative sizes, bad layouts, bad SELL parameters, null output
+    assert lib.bcs_csr_upload(-1, 0, rp.ctypes.data, None, None, 1, 32, 256, 1, None, ctypes.byref(h)) == bcs.ERR_ARG
+    assert lib.bcs_csr_upload(1, 1, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0, 32, 256, 1, None,
+                              ctypes.byref(h)) == bcs.ERR_ARG
+    assert lib.bcs_csr_upload(1, 1, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 2, 16, 256, 1, None,
+                              ctypes.byref(h)) == bcs.ERR_ARG
+    assert lib.bcs_csr_upload(1, 1, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 2, 32, 100, 1, None,
+                              ctypes.byref(h)) == bcs.ERR_ARG
+    assert lib.bcs_csr_upload(1, 1, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 1, 32, 256, 1, None,
+                              None) == bcs.ERR_ARG
+    assert lib.bcs_csr_upload(1, 1, rp.ctypes.data, None, None, 1, 32, 256, 1, None, ctypes.byref(h)) == bcs.ERR_ARG
+    o = bcs.options()
+    assert lib.bcs_solver_create(None, 0, 1e-8, 10, ctypes.byref(o), ctypes.byref(h)) == bcs.ERR_ARG
+    assert lib.bcs_solve(None, None, None, None, None) == bcs.ERR_ARG
+    assert lib.bcs_solve_host(None, None, None, None, None) == bcs.ERR_ARG
+    assert lib.bcs_get_history(None, None, 0, None) == bcs.ERR_ARG
+    assert lib.bcs_spmv(None, 1, 1, None, None, 0, 0, None) == bcs.ERR_ARG
+    assert lib.bcs_solve_batched(-1, None, 0, 1e-8, 10, None, None, None, None, None) == bcs.ERR_ARG
+    assert lib.bcs_solve_batched(0, None, 0, 1e-8, 10, None, None, None, None, None) == bcs.OK
+    assert lib.bcs_solve_batched(1, None, 7, 1e-8, 10, None, None, None, None, None) == bcs.ERR_ARG
+    lib.bcs_matrix_free(None)
+    lib.bcs_solver_destroy(None)
