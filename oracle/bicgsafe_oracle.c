@@ -37,7 +37,9 @@
  * Arithmetic: every multiply-add that the listing writes as "a + b*c" is one
  * C99 fma() (correctly rounded); nothing else is contracted (the file is
  * compiled with -ffp-contract=off).  SpMV sums a row's entries sequentially in
- * storage order.  Inner products use pairwise summation (blocks of 8).
+ * storage order.  Inner products are correctly rounded (exact sum of exact
+ * products, rounded once): the paper writes them as the mathematical (x, y)
+ * and fixes no summation order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -86,16 +88,102 @@ void orc_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double
     }
 }
 
-/* Pairwise-summed inner product (x, y). */
+/*
+ * Inner product (x, y) = sum_i x_i y_i, correctly rounded: every product is
+ * formed exactly (53 x 53-bit integer product) and added exactly into a
+ * fixed-point integer wide enough for the whole FP64 product range; the exact
+ * sum is rounded once, to nearest even.  The result therefore does not depend
+ * on the order of the terms.  Any NaN or infinity among the inputs falls back
+ * to the plain left-to-right sum so that it propagates as IEEE arithmetic does.
+ */
+#define XB_LIMBS 70          /* 4480 bits */
+#define XB_BIAS 2240         /* bit index of 2^0 */
+typedef struct { uint64_t l[XB_LIMBS]; } bigfix;
+
+static void big_addsub(bigfix* a, int limb, uint64_t v, int neg)
+{
+    /* a += v * 2^(64*limb) or a -= v * 2^(64*limb), two's complement */
+    for (int k = limb; k < XB_LIMBS && (v != 0 || neg == 2); ++k) {
+        if (!neg) {
+            uint64_t o = a->l[k];
+            a->l[k] = o + v;
+            v = (a->l[k] < o) ? 1 : 0;
+        } else {
+            uint64_t o = a->l[k];
+            a->l[k] = o - v;
+            v = (o < v) ? 1 : 0;
+        }
+    }
+}
+
+static void split(double v, uint64_t* m, int* e)
+{
+    uint64_t b; memcpy(&b, &v, 8);
+    int E = (int)((b >> 52) & 0x7FF);
+    *m = b & 0xFFFFFFFFFFFFFull;
+    if (E) { *m |= 1ull << 52; *e = E - 1075; } else { *e = -1074; }
+}
+
+static double big_round(const bigfix* a0)
+{
+    bigfix a = *a0;
+    int neg = (int)(a.l[XB_LIMBS - 1] >> 63);
+    if (neg) { /* negate */
+        int carry = 1;
+        for (int k = 0; k < XB_LIMBS; ++k) {
+            uint64_t v = ~a.l[k];
+            a.l[k] = v + (uint64_t)carry;
+            carry = carry && a.l[k] == 0;
+        }
+    }
+    int top = -1;
+    for (int k = XB_LIMBS - 1; k >= 0; --k)
+        if (a.l[k]) { top = 64 * k + 63 - __builtin_clzll(a.l[k]); break; }
+    if (top < 0) return 0.0;
+    int exp_msb = top - XB_BIAS;                   /* value in [2^exp_msb, 2^(exp_msb+1)) */
+    int lsb = (exp_msb >= -1022) ? top - 52 : -1074 + XB_BIAS;  /* lowest kept bit (absolute) */
+    /* kept bits [lsb, top] (at most 53), round bit lsb-1, sticky below */
+    uint64_t mant = 0;
+    for (int p = top; p >= lsb; --p) mant = (mant << 1) | ((a.l[p / 64] >> (p % 64)) & 1u);
+    int rbit = (lsb - 1 >= 0) ? (int)((a.l[(lsb - 1) / 64] >> ((lsb - 1) % 64)) & 1u) : 0;
+    int sticky = 0;
+    for (int p = lsb - 2; p >= 0 && !sticky; --p) {
+        if (p % 64 == 63 && a.l[p / 64] == 0) { p -= 63; continue; }
+        sticky = (int)((a.l[p / 64] >> (p % 64)) & 1u);
+    }
+    if (rbit && (sticky || (mant & 1u))) mant += 1;
+    double r = ldexp((double)mant, lsb - XB_BIAS);  /* exact: mant < 2^54 and fits the format */
+    return neg ? -r : r;
+}
+
 double orc_dot(int64_t n, const double* x, const double* y)
 {
-    if (n <= 8) {
-        double s = 0.0;
-        for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
-        return s;
+    bigfix a;
+    memset(&a, 0, sizeof(a));
+    for (int64_t i = 0; i < n; ++i) {
+        if (!isfinite(x[i]) || !isfinite(y[i])) {
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j) s += x[j] * y[j];
+            return s;
+        }
+        uint64_t mx, my;
+        int ex, ey;
+        split(x[i], &mx, &ex);
+        split(y[i], &my, &ey);
+        if (mx == 0 || my == 0) continue;
+        unsigned __int128 p = (unsigned __int128)mx * my;
+        int neg = (signbit(x[i]) != 0) != (signbit(y[i]) != 0);
+        int pos = ex + ey + XB_BIAS;               /* bit index of the product's bit 0 */
+        int limb = pos / 64, sh = pos % 64;
+        uint64_t lo = (uint64_t)p, hi = (uint64_t)(p >> 64);
+        uint64_t v0 = lo << sh;
+        uint64_t v1 = sh ? ((lo >> (64 - sh)) | (hi << sh)) : hi;
+        uint64_t v2 = sh ? (hi >> (64 - sh)) : 0;
+        big_addsub(&a, limb, v0, neg);
+        big_addsub(&a, limb + 1, v1, neg);
+        big_addsub(&a, limb + 2, v2, neg);
     }
-    int64_t h = n / 2;
-    return orc_dot(h, x, y) + orc_dot(n - h, x + h, y + h);
+    return big_round(&a);
 }
 
 /* ||b - A x||_2, computed with the routines above. */
