@@ -74,10 +74,14 @@ typedef struct {
     int max_outer;        /* outer steps: true-residual checks / restarts / refinement steps (default 30) */
     int history_len;      /* capacity of the residual history (default 4096 entries) */
     int layout;           /* BCS_LAYOUT_CSR (default) or BCS_LAYOUT_SELL; must have been uploaded */
-    int threads_per_row;  /* CSR only: 1,2,4,8,16 or 32 lanes per row; 0 = chosen from the row lengths */
+    int threads_per_row;  /* CSR only: 1, 4, 8 or 32 lanes per row; 0 = the library's choice (1) */
     int ctas_per_sm;      /* 0 = chosen by occupancy; otherwise 1..8 */
     int max_ctas;         /* 0 = no cap; otherwise an upper bound on the grid size */
     double spin_budget_ms;/* per grid-barrier wait before BCS_ERR_TIMEOUT (default 2000 ms) */
+    int inner_maxit;      /* refinement modes: at most this many iterations per inner run (0 = no cap) */
+    int inner_stall;      /* refinement modes: end an inner run after this many iterations without a new
+                             smallest recursive residual (default 50; 0 = off); the FP64 outer step
+                             then recomputes the true residual and starts a fresh Krylov space */
 } bcs_options;
 
 typedef struct {
@@ -140,12 +144,28 @@ int bcs_matrix_export(bcs_matrix A, int32_t* rowptr, int32_t* col, double* val64
  *   store   BCS_STORE_F64 / F32 / BF16: which value copy to use.
  *   x, y    device vectors of n elements in original row order, FP64 when
  *           vec_f32 == 0, FP32 otherwise; x and y must not overlap.
- *   threads_per_row  CSR lanes per row (1,2,4,8,16,32; 0 = automatic).
+ *   threads_per_row  CSR lanes per row (1, 4, 8, 32; 0 = automatic).
  * Rows are summed with fused multiply-adds; with one lane per row (and for
  * SELL) in storage order.  Asynchronous on stream.
  */
 int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int vec_f32,
              int threads_per_row, void* stream);
+
+/*
+ * Correctly rounded inner product (x, y) = sum_i x_i y_i of two device
+ * vectors: the a_i ... r_i of Algorithms 3-5, computed the way the solver
+ * computes them.  Each product is formed exactly as an integer and
+ * accumulated in 128-bit fixed point on the integer units; the sum is rounded
+ * once to nearest even, so the result does not depend on the order of the
+ * terms or the launch configuration (bits more than 2^-110 below the largest
+ * term are dropped, which changes the result only when the sum cancels by a
+ * factor of more than about 2^50).
+ *   n        number of elements (>= 0).
+ *   x, y     device vectors, FP64 when vec_f32 == 0, FP32 otherwise.
+ *   result   host double receiving the value (a NaN or Inf operand gives NaN).
+ * Synchronises the stream; allocates and frees a small device buffer.
+ */
+int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result, void* stream);
 
 /* Free a matrix (NULL is ignored).  Waits for the device first. */
 void bcs_matrix_free(bcs_matrix A);

@@ -25,7 +25,7 @@ LAYOUT_CSR, LAYOUT_SELL = 1, 2
 STORE_F64, STORE_F32, STORE_BF16 = 1, 2, 4
 OK, NOT_CONVERGED, ERR_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NONFINITE, ERR_OOM = 0, 1, -1, -2, -3, -4, -5, -6
 
-EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv",
+EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv", "bcs_dot",
             "bcs_matrix_free", "bcs_solver_create", "bcs_solve", "bcs_solve_host", "bcs_get_history",
             "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_status_string"]
 
@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("rr_m", ctypes.c_int), ("rr_M", ctypes.c_int), ("precision", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("history_len", ctypes.c_int),
                 ("layout", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("max_ctas", ctypes.c_int), ("spin_budget_ms", ctypes.c_double)]
+                ("max_ctas", ctypes.c_int), ("spin_budget_ms", ctypes.c_double), ("inner_maxit", ctypes.c_int),
+                ("inner_stall", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -61,6 +62,7 @@ def _load():
                                   ctypes.POINTER(I), ctypes.POINTER(I)]
     L.bcs_matrix_export.argtypes = [P] * 10
     L.bcs_spmv.argtypes = [P, I, I, P, P, I, I, P]
+    L.bcs_dot.argtypes = [I64, P, P, I, ctypes.POINTER(D), P]
     L.bcs_matrix_free.argtypes = [P]
     L.bcs_matrix_free.restype = None
     L.bcs_solver_create.argtypes = [P, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
@@ -203,6 +205,15 @@ def spmv(M, x, y, layout=LAYOUT_CSR, store=STORE_F64, threads_per_row=0, stream=
     _check(lib.bcs_spmv(M.handle, layout, store, _ptr(x), _ptr(y), int(f32), threads_per_row, _stream(stream)),
            "bcs_spmv")
     return y
+
+
+def dot(x, y, stream=None):
+    """bcs_dot: correctly rounded (x, y) of two torch CUDA tensors (float64 or float32)."""
+    import torch
+    out = ctypes.c_double()
+    _check(lib.bcs_dot(x.numel(), _ptr(x), _ptr(y), int(x.dtype == torch.float32), ctypes.byref(out),
+                       _stream(stream)), "bcs_dot")
+    return out.value
 
 
 class Solver:

@@ -11,9 +11,13 @@
 using namespace bcs;
 
 namespace bcs {
-int dispatch_f64(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
-int dispatch_f32(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
-int dispatch_bf16(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
+#define BCS_DECL(tag)                                                                                  \
+    int dispatch_##tag##_0(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid); \
+    int dispatch_##tag##_1(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
+BCS_DECL(f64)
+BCS_DECL(f32)
+BCS_DECL(bf16)
+#undef BCS_DECL
 int dispatch_batched_f64(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
 int dispatch_batched_f32(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
 int dispatch_batched_bf16(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
@@ -23,9 +27,11 @@ int default_tpr(const bcs_matrix_s* A);
 namespace {
 
 int dispatch(const KParams* P, int vt_f32, int valtype, int layout, int tpr, int grid, cudaStream_t st, int* mg) {
-    if (!vt_f32) return dispatch_f64(P, layout, tpr, grid, st, mg);
-    if (valtype == VAL_F32) return dispatch_f32(P, layout, tpr, grid, st, mg);
-    return dispatch_bf16(P, layout, tpr, grid, st, mg);
+    const bool sub0 = layout == LAY_SELL || tpr == 1;
+    if (!vt_f32) return sub0 ? dispatch_f64_0(P, layout, tpr, grid, st, mg) : dispatch_f64_1(P, layout, tpr, grid, st, mg);
+    if (valtype == VAL_F32)
+        return sub0 ? dispatch_f32_0(P, layout, tpr, grid, st, mg) : dispatch_f32_1(P, layout, tpr, grid, st, mg);
+    return sub0 ? dispatch_bf16_0(P, layout, tpr, grid, st, mg) : dispatch_bf16_1(P, layout, tpr, grid, st, mg);
 }
 
 int dispatch_b(const BatchArgs* B, int vt_f32, int valtype, int tpr, int nc, cudaStream_t st, int* mc) {
@@ -34,7 +40,7 @@ int dispatch_b(const BatchArgs* B, int vt_f32, int valtype, int tpr, int nc, cud
     return dispatch_batched_bf16(B, tpr, nc, st, mc);
 }
 
-bool valid_tpr(int t) { return t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32; }
+bool valid_tpr(int t) { return t == 1 || t == 4 || t == 8 || t == 32; }
 
 long long budget_cycles(double ms) {
     // SM cycles per millisecond at the GB300's maximum SM clock (2070 MHz);
@@ -72,6 +78,7 @@ int check_options(const bcs_options& o) {
     if (o.threads_per_row != 0 && !valid_tpr(o.threads_per_row)) return BCS_ERR_ARG;
     if (o.ctas_per_sm < 0 || o.ctas_per_sm > 8 || o.max_ctas < 0) return BCS_ERR_ARG;
     if (!(o.spin_budget_ms > 0.0)) return BCS_ERR_ARG;
+    if (o.inner_maxit < 0 || o.inner_stall < 0) return BCS_ERR_ARG;
     return BCS_OK;
 }
 
@@ -93,6 +100,8 @@ void bcs_options_default(bcs_options* o) {
     o->ctas_per_sm = 0;
     o->max_ctas = 0;
     o->spin_budget_ms = 2000.0;
+    o->inner_maxit = 0;
+    o->inner_stall = 50;
 }
 
 const char* bcs_status_string(int s) {
@@ -166,14 +175,14 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
         alloc((void**)&s->x64w, sizeof(double) * nn);
         alloc((void**)&s->b64w, sizeof(double) * nn);
     }
-    alloc((void**)&s->partials, sizeof(double) * 2 * (size_t)grid * NSLOT);
+    alloc((void**)&s->partials, sizeof(double) * 2 * (size_t)grid * NSLOT * kRec);
     alloc((void**)&s->bar, 64);
     alloc((void**)&s->hist, sizeof(double) * std::max(o.history_len, 1));
     alloc((void**)&s->scal, sizeof(double) * 4 * std::max(o.history_len, 1));
     alloc((void**)&s->out, sizeof(double) * NOUT);
     if (!rc && cudaMallocHost((void**)&s->host_out, sizeof(double) * NOUT + 64) != cudaSuccess) rc = BCS_ERR_OOM;
     if (!rc && (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess)) rc = BCS_ERR_CUDA;
-    if (!rc && cudaMemset(s->partials, 0, sizeof(double) * 2 * (size_t)grid * NSLOT) != cudaSuccess) rc = BCS_ERR_CUDA;
+    if (!rc && cudaMemset(s->partials, 0, sizeof(double) * 2 * (size_t)grid * NSLOT * kRec) != cudaSuccess) rc = BCS_ERR_CUDA;
     if (rc) {
         bcs_solver_destroy(s);
         return rc;
@@ -194,6 +203,8 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
     P->max_outer = s->opt.max_outer;
     P->mixed = s->vt_f32;
     P->hist_cap = s->opt.history_len;
+    P->inner_maxit = s->opt.inner_maxit;
+    P->inner_stall = s->opt.inner_stall;
     P->tol = s->tol;
     P->inner_tol = s->opt.inner_tol;
     P->spin_budget = budget_cycles(s->opt.spin_budget_ms);
@@ -340,9 +351,10 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
     int tpr = o.threads_per_row;
     if (!tpr) {
         const double avg = sum_avg / nsys;
-        tpr = avg <= 1.0 ? 1 : avg <= 4.0 ? 4 : avg <= 8.0 ? 8 : 32;
+        tpr = vt_f32 ? 8 : 1;  // FP64: one lane per row keeps shuffle-adds off the FP64 units
+        (void)avg;
     }
-    if (tpr != 1 && tpr != 4 && tpr != 8 && tpr != 32) return BCS_ERR_ARG;
+    if (tpr != 1 && tpr != 8) return BCS_ERR_ARG;
     const int csize = o.ctas_per_sm > 0 ? o.ctas_per_sm : 4;  // CTAs per cluster
     if (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -377,7 +389,7 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
     ck(cudaMalloc(&dorder, sizeof(int) * nsys));
     ck(cudaMalloc(&dctl, sizeof(int) * (1 + nclusters)));
     if (!rc && cudaMalloc(&ws, B.ws_group_bytes * nclusters) != cudaSuccess) rc = BCS_ERR_OOM;
-    ck(cudaMalloc(&parts, sizeof(double) * 2 * NSLOT * csize * nclusters));
+    ck(cudaMalloc(&parts, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters));
     ck(cudaMalloc(&outs, sizeof(double) * NOUT * nsys));
     if (!rc) {
         for (int k = 0; k < nsys; ++k) {
@@ -393,6 +405,8 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
             P.max_outer = o.max_outer;
             P.mixed = vt_f32;
             P.hist_cap = 0;
+            P.inner_maxit = o.inner_maxit;
+            P.inner_stall = o.inner_stall;
             P.tol = tol;
             P.inner_tol = o.inner_tol;
             P.rowptr = M->rowptr;
@@ -409,7 +423,7 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
         ck(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
         ck(cudaMemsetAsync(dctl, 0, sizeof(int) * (1 + nclusters), st));
         ck(cudaMemsetAsync(outs, 0, sizeof(double) * NOUT * nsys, st));
-        ck(cudaMemsetAsync(parts, 0, sizeof(double) * 2 * NSLOT * csize * nclusters, st));
+        ck(cudaMemsetAsync(parts, 0, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters, st));
         ck(cudaEventCreate(&e0));
         ck(cudaEventCreate(&e1));
     }

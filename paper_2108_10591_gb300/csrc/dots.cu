@@ -1,0 +1,57 @@
+// bcs_dot: the correctly rounded inner product on the device (the primitive
+// behind the solver's a_i ... r_i), as a standalone entry point.
+#include <string.h>
+
+#include <algorithm>
+
+#include "solver.cuh"
+
+using namespace bcs;
+
+namespace {
+
+template <class VT>
+__global__ void __launch_bounds__(kBlock) k_dot_partial(int64_t n, const VT* x, const VT* y, unsigned long long* recs) {
+    __shared__ XStage s_x;
+    XAcc a[10];
+    xa_init10(a);
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
+        xa_acc(a[0], x[i], y[i]);
+    flush_partials<1u>(a, s_x, recs + (size_t)blockIdx.x * NSLOT * kRec);
+}
+
+__global__ void __launch_bounds__(kBlock) k_dot_final(const unsigned long long* recs, int nblk, double* out) {
+    __shared__ XStage s_x;
+    __shared__ double s_out[10];
+    reduce_partials(recs, nblk, s_x, s_out);
+    if (threadIdx.x == 0) *out = s_out[0];
+}
+
+}  // namespace
+
+extern "C" int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result, void* stream) {
+    if (n < 0 || !result || (n > 0 && (!x || !y))) return BCS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)sms * 4));
+    unsigned long long* recs = nullptr;
+    double* dout = nullptr;
+    int rc = BCS_OK;
+    if (cudaMalloc(&recs, sizeof(unsigned long long) * (size_t)nblk * NSLOT * kRec) != cudaSuccess ||
+        cudaMalloc(&dout, sizeof(double)) != cudaSuccess) {
+        rc = BCS_ERR_OOM;
+    } else {
+        if (vec_f32) k_dot_partial<float><<<nblk, kBlock, 0, st>>>(n, (const float*)x, (const float*)y, recs);
+        else k_dot_partial<double><<<nblk, kBlock, 0, st>>>(n, (const double*)x, (const double*)y, recs);
+        k_dot_final<<<1, kBlock, 0, st>>>(recs, nblk, dout);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(result, dout, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = BCS_ERR_CUDA;
+    }
+    if (recs) cudaFree(recs);
+    if (dout) cudaFree(dout);
+    return rc;
+}

@@ -28,6 +28,7 @@ struct KParams {
     int64_t n;
     int64_t ntiles;         // 32-row tiles
     int kind, maxit, rr_m, rr_M, max_outer, mixed, hist_cap;
+    int inner_maxit, inner_stall;  // refinement modes: inner-run cap and stall window (0 = off)
     double tol, inner_tol;
     long long spin_budget;  // clock64 cycles per barrier wait
     // matrix: CSR (rowptr, col, val) or SELL (slice_ptr, col=scol, val=sval, perm)
@@ -45,18 +46,13 @@ struct KParams {
     const double* b64;
     double* b64w;           // SELL: writable permuted copy of b
     void* vec[NVEC];
-    double* partials;       // [2][gridDim.x][NSLOT]
+    double* partials;       // exact partial records: [2][CTAs][NSLOT][3] 64-bit words
     unsigned* bar;          // barrier counter, zero at launch
     int* err;               // error flag, zero at launch
     double* hist;           // [hist_cap]
     double* scal;           // [4*hist_cap]
     double* out;            // [NOUT]
 };
-
-// solver kernel launchers (solver_*.cu); return a cudaError_t as int
-int launch_solver(const KParams& P, int vt_f32, int valtype, int layout, int tpr, int grid,
-                  cudaStream_t st, int* max_grid_out);
-int solver_max_grid(int vt_f32, int valtype, int layout, int tpr, int* grid);
 
 }  // namespace bcs
 

@@ -209,10 +209,8 @@ int spmv_launch(bcs_matrix A, int layout, const MT* val, const VT* x, VT* y, int
         P.col = A->col;
         switch (tpr) {
             case 1: k_spmv<VT, MT, LAY_CSR, 1><<<grid, 256, 0, st>>>(P, val, x, y); break;
-            case 2: k_spmv<VT, MT, LAY_CSR, 2><<<grid, 256, 0, st>>>(P, val, x, y); break;
             case 4: k_spmv<VT, MT, LAY_CSR, 4><<<grid, 256, 0, st>>>(P, val, x, y); break;
             case 8: k_spmv<VT, MT, LAY_CSR, 8><<<grid, 256, 0, st>>>(P, val, x, y); break;
-            case 16: k_spmv<VT, MT, LAY_CSR, 16><<<grid, 256, 0, st>>>(P, val, x, y); break;
             default: k_spmv<VT, MT, LAY_CSR, 32><<<grid, 256, 0, st>>>(P, val, x, y); break;
         }
     }
@@ -222,12 +220,12 @@ int spmv_launch(bcs_matrix A, int layout, const MT* val, const VT* x, VT* y, int
 }  // namespace
 
 namespace bcs {
-// Lanes per CSR row from the mean row length (smallest power of two >= mean, at most 32).
+// Lanes per CSR row when the caller does not choose: the autotuned value if
+// there is one, else one lane per row (no cross-lane reduction: on GB300 an
+// FP64 shuffle-add costs an FP64-pipe slot like an FMA).
 int default_tpr(const bcs_matrix_s* A) {
     if (A->tuned_tpr) return A->tuned_tpr;
-    int t = 1;
-    while (t < 32 && t < A->avg_row) t *= 2;
-    return t;
+    return 1;
 }
 }  // namespace bcs
 
@@ -382,7 +380,7 @@ int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int ve
     if (store != BCS_STORE_F64 && store != BCS_STORE_F32 && store != BCS_STORE_BF16) return BCS_ERR_ARG;
     if (!vec_f32 && store != BCS_STORE_F64) return BCS_ERR_ARG;  // FP64 vectors use the FP64 values
     int tpr = threads_per_row ? threads_per_row : default_tpr(A);
-    if (tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32) return BCS_ERR_ARG;
+    if (tpr != 1 && tpr != 4 && tpr != 8 && tpr != 32) return BCS_ERR_ARG;
     if (A->n == 0) return BCS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const bool sell = layout == BCS_LAYOUT_SELL;

@@ -34,8 +34,116 @@
 #include <math.h>
 
 #include "device.cuh"
+#include "xacc.cuh"
 
 namespace bcs {
+
+// ---- exact inner-product partials ------------------------------------------------------
+// Per-CTA records: NSLOT slots x (anchor, hi, lo) as three 64-bit words.
+constexpr int kRec = 3;
+
+__device__ __forceinline__ void xa_init10(XAcc (&a)[10]) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) xa_init(a[k]);
+}
+
+// Shared scratch of the block-level merges: every thread stages up to kStage
+// accumulators; the merge then loops over slots at run time (one copy of the
+// merge code instead of one per slot and call site).
+constexpr int kStage = 5;
+struct XStage {
+    XAcc v[kStage][kBlock];
+    XAcc w[kStage][kWarps];
+};
+
+// Merge the staged accumulators v[0..ns) over the block: warp butterflies, then
+// one more over the per-warp results.  Result of slot j in v[j][0].
+__device__ __forceinline__ void xa_block_merge(XStage& st, int ns) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __syncthreads();
+#pragma unroll 1
+    for (int j = 0; j < ns; ++j) {
+        XAcc a = st.v[j][t];
+        xa_warp_merge(a);
+        if (lane == 0) st.w[j][warp] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll 1
+        for (int j = 0; j < ns; ++j) {
+            XAcc a;
+            if (lane < kWarps) a = st.w[j][lane]; else xa_init(a);
+            xa_warp_merge(a);
+            if (lane == 0) st.v[j][0] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// Merge the CTA's accumulators of the slots in MASK (at most kStage) and store
+// them as the CTA's record; slots in ZMASK are recorded as empty (zero).
+template <unsigned MASK, unsigned ZMASK = 0u>
+__device__ __forceinline__ void flush_partials(XAcc (&a)[10], XStage& st, unsigned long long* rec) {
+    static_assert(__builtin_popcount(MASK) <= kStage, "too many slots");
+    {
+        int j = 0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+            if ((MASK >> k) & 1u) st.v[j++][threadIdx.x] = a[k];
+    }
+    xa_block_merge(st, __builtin_popcount(MASK));
+    if (threadIdx.x == 0) {
+        int j = 0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            if ((MASK >> k) & 1u) {
+                const XAcc& t = st.v[j++][0];
+                rec[k * kRec + 0] = (unsigned long long)(long long)t.e;
+                rec[k * kRec + 1] = t.hi;
+                rec[k * kRec + 2] = t.lo;
+            } else if ((ZMASK >> k) & 1u) {
+                rec[k * kRec + 0] = (unsigned long long)(long long)kXaEmpty;
+                rec[k * kRec + 1] = 0;
+                rec[k * kRec + 2] = 0;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Pull this thread's share of the partial records into L1 ahead of use.
+__device__ __forceinline__ void prefetch_partials(const unsigned long long* base, int nblk) {
+    for (int c = threadIdx.x; c < nblk; c += kBlock) {
+        const char* r = (const char*)(base + (size_t)c * NSLOT * kRec);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(r + 128));
+    }
+}
+
+// Sum every CTA's record (the same order in every CTA, so all CTAs obtain the
+// same values) and round each slot once: out[k] = correctly rounded slot k.
+__device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage& st, double* out) {
+#pragma unroll 1
+    for (int k0 = 0; k0 < 10; k0 += kStage) {
+#pragma unroll 1
+        for (int j = 0; j < kStage; ++j) {
+            XAcc a;
+            xa_init(a);
+            for (int c = threadIdx.x; c < nblk; c += kBlock) {
+                const unsigned long long* r = base + (size_t)c * NSLOT * kRec + (k0 + j) * kRec;
+                XAcc t;
+                t.e = (int)(long long)r[0];
+                t.hi = r[1];
+                t.lo = r[2];
+                xa_merge(a, t);
+            }
+            st.v[j][threadIdx.x] = a;
+        }
+        xa_block_merge(st, kStage);
+        if (threadIdx.x < kStage) out[k0 + threadIdx.x] = xa_round(st.v[threadIdx.x][0]);
+        __syncthreads();
+    }
+}
 
 // A set of CTAs that solve one system together: the whole cooperative grid
 // (one large system) or one thread-block cluster (batched solves).
@@ -57,9 +165,8 @@ struct ClusterGroup {
 
 template <class VT, class MT, int LAYOUT, int T, class Group>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
-    __shared__ double s_red[kWarps * 10];
+    __shared__ XStage s_x;
     __shared__ double s_sum[10];
-    __shared__ double s_tmp[10];
     __shared__ double s_sc[4];
     __shared__ int s_ctl[2];
     __shared__ int s_flag;
@@ -102,30 +209,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     auto spmv64 = [&](const double* xv, int64_t tile) -> double {
         return tile_spmv<double, double, LAYOUT, T>(P, P.val64, xv, tile, sbuf64);
     };
-    auto pslot = [&](int buf, int c, int k) -> double* {
-        return P.partials + ((size_t)buf * nblk + c) * NSLOT + k;
-    };
-    auto zero10 = [](double (&v)[10]) {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) v[k] = 0.0;
-    };
-    // Sum the CTA's per-thread partials and store the slots in `mask`.
-    auto flush = [&](int buf, double (&v)[10], unsigned mask) {
-        block_sum<10>(v, s_red, s_tmp);
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < 10; ++k)
-                if ((mask >> k) & 1u) *pslot(buf, rank, k) = s_tmp[k];
-        }
-    };
-    auto load_partials = [&](int buf, double (&v)[10]) {
-        zero10(v);
-        for (int c = threadIdx.x; c < nblk; c += kBlock) {
-            const double* src = pslot(buf, c, 0);
-#pragma unroll
-            for (int k = 0; k < 10; ++k) v[k] += src[k];
-        }
-    };
-    auto dacc = [](double& acc, VT a, VT b) { acc = fma((double)a, (double)b, acc); };
+    unsigned long long* const precs = (unsigned long long*)P.partials;
+    auto rbase = [&](int buf) -> unsigned long long* { return precs + (size_t)buf * nblk * NSLOT * kRec; };
+    auto myrec = [&](int buf) -> unsigned long long* { return rbase(buf) + (size_t)rank * NSLOT * kRec; };
 
     // ---- SELL: the solve runs in the permuted row order ----
     if (P.perm != nullptr) {
@@ -144,18 +230,20 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     int total = 0, evals = 0, runs = 0, hist_len = 0, rr_steps = 0, fallbacks = 0;
     double r0n = 0.0, thresh = 0.0, r0ref = 1.0, rtrue = 0.0, last_rec = 0.0;
     double alpha_p = 0.0, zeta_p = 0.0, f_p = 0.0;  // thread 0 of each CTA
+    double best_rn = 0.0;                            // refinement modes: stall guard (thread 0)
+    int since_best = 0;
 
     for (;;) {
         // ---------------- true residual r = b - A x (FP64) and (re)initialisation ----------
         {
-            double pv[10];
-            zero10(pv);
+            XAcc xv[10];
+            xa_init10(xv);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const double ax = spmv64(P.x64, tile);
                 const int64_t row = tile * 32 + lane;
                 if (row < n) {
                     const double r64 = P.b64[row] - ax;
-                    pv[ST] = fma(r64, r64, pv[ST]);
+                    xa_fma64(xv[ST], r64, r64);
                     const VT rv = (VT)r64;
                     R[row] = rv;
                     RS[row] = rv;
@@ -165,14 +253,15 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     }
                     Y[row] = VT(0); Tv[row] = VT(0); Pv[row] = VT(0); U[row] = VT(0);
                     Z[row] = VT(0); W[row] = VT(0); L[row] = VT(0); G[row] = VT(0);
-                    dacc(pv[SF], rv, rv);
+                    xa_acc(xv[SF], rv, rv);
                 }
             }
-            pv[SR] = pv[SF];
-            flush(0, pv, (1u << ST) | (1u << SF) | (1u << SR) | (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH));
+            xv[SR] = xv[SF];
+            flush_partials<(1u << ST) | (1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(
+                xv, s_x, myrec(0));
             if (!grp.sync(&s_flag)) return;
-            load_partials(0, pv);
-            block_sum<10>(pv, s_red, s_sum);
+            prefetch_partials(rbase(0), nblk);
+            reduce_partials(rbase(0), nblk, s_x, s_sum);
             const double rt2 = s_sum[ST];
             rtrue = sqrt(rt2);
             if (evals == 0) {
@@ -191,20 +280,20 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 
         // ---------------- pipelined set-up: s_0 = A r_0 and the i = 0 products --------------
         if (kind != BCS_SSBICGSAFE2) {
-            double pv[10];
-            zero10(pv);
+            XAcc xv[10];
+            xa_init10(xv);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const VT sv = spmv(R, tile);
                 const int64_t row = tile * 32 + lane;
                 if (row < n) {
                     sCur[row] = sv;
                     const VT rv = R[row], rsv = RS[row];
-                    dacc(pv[SA], sv, sv);
-                    dacc(pv[SD], sv, rv);
-                    dacc(pv[SG], rsv, sv);
+                    xa_acc(xv[SA], sv, sv);
+                    xa_acc(xv[SD], sv, rv);
+                    xa_acc(xv[SG], rsv, sv);
                 }
             }
-            flush(0, pv, (1u << SA) | (1u << SD) | (1u << SG));
+            flush_partials<(1u << SA) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(0));
             if (!grp.sync(&s_flag)) return;
         }
 
@@ -213,32 +302,33 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         for (;; ++i) {
             const int cur = i & 1, nxt = cur ^ 1;
             const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
-            double pv[10];
+            XAcc xv[10];
             VT as_first = VT(0);
             if (kind == BCS_SSBICGSAFE2) {
                 // phase A: s_i = A r_i and the products involving s_i
-                zero10(pv);
+                xa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT sv = spmv(R, tile);
                     const int64_t row = tile * 32 + lane;
                     if (row < n) {
                         sCur[row] = sv;
                         const VT yv = Y[row], rv = R[row], rsv = RS[row];
-                        dacc(pv[SA], sv, sv);
-                        dacc(pv[SC], sv, yv);
-                        dacc(pv[SD], sv, rv);
-                        dacc(pv[SG], rsv, sv);
+                        xa_acc(xv[SA], sv, sv);
+                        xa_acc(xv[SC], sv, yv);
+                        xa_acc(xv[SD], sv, rv);
+                        xa_acc(xv[SG], rsv, sv);
                     }
                 }
-                flush(cur, pv, (1u << SA) | (1u << SC) | (1u << SD) | (1u << SG));
+                flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(cur));
                 if (!grp.sync(&s_flag)) return;
-                load_partials(cur, pv);
+                prefetch_partials(rbase(cur), nblk);
             } else {
-                // phase A: the reduction of iteration i overlaps A s_i of the first tile
-                load_partials(cur, pv);
+                // phase A: the partials of iteration i travel to L1 while A s_i of the
+                // first tile is computed (the overlap of the reduction with MV, Section 3)
+                prefetch_partials(rbase(cur), nblk);
                 if (!rr_step && gwarp < ntiles) as_first = spmv(sCur, gwarp);
             }
-            block_sum<10>(pv, s_red, s_sum);
+            reduce_partials(rbase(cur), nblk, s_x, s_sum);
 
             // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
             if (threadIdx.x == 0) {
@@ -268,6 +358,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 const double rn = sqrt(rr);
                 const bool conv = rn <= thr_in;
+                if (i == 0 || rn < best_rn) { best_rn = rn; since_best = 0; } else { ++since_best; }
                 int dec = 0, st = BCS_OK;
                 if (brk && !conv) {
                     dec = 1;
@@ -286,6 +377,12 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     else if (!isfinite(alpha) || !isfinite(beta) || !isfinite(zeta) || !isfinite(eta) || !isfinite(rr)) {
                         dec = 1; st = BCS_ERR_NONFINITE;
                     } else if (i >= budget) { dec = 1; st = BCS_NOT_CONVERGED; }
+                    else if (mixed && ((P.inner_maxit > 0 && i >= P.inner_maxit) ||
+                                       (P.inner_stall > 0 && since_best >= P.inner_stall))) {
+                        // low-precision inner run capped or no longer improving: hand
+                        // back to the FP64 outer step (true residual, fresh Krylov space)
+                        dec = 1; st = BCS_OK;
+                    }
                 }
                 s_sc[0] = alpha; s_sc[1] = beta; s_sc[2] = zeta; s_sc[3] = eta;
                 s_ctl[0] = dec; s_ctl[1] = st;
@@ -310,7 +407,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 if (!grp.sync(&s_flag)) return;
                 // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
-                zero10(pv);
+                xa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT w = spmv(U, tile);
                     const int64_t row = tile * 32 + lane;
@@ -323,18 +420,18 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         x = vfma(al, p, x) + z;
                         const VT rn = vfma(-al, o, r) - yn;
                         Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x; R[row] = rn;
-                        dacc(pv[SB], yn, yn);
-                        dacc(pv[SE], yn, rn);
-                        dacc(pv[SF], rs, rn);
-                        dacc(pv[SH], rs, t);
-                        dacc(pv[SR], rn, rn);
+                        xa_acc(xv[SB], yn, yn);
+                        xa_acc(xv[SE], yn, rn);
+                        xa_acc(xv[SF], rs, rn);
+                        xa_acc(xv[SH], rs, t);
+                        xa_acc(xv[SR], rn, rn);
                     }
                 }
-                flush(nxt, pv, (1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR));
+                flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
             } else if (!rr_step) {
                 // phase A (continued): fused recurrences of Alg. 4
-                zero10(pv);
+                xa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT As = (tile == gwarp) ? as_first : spmv(sCur, tile);
                     const int64_t row = tile * 32 + lane;
@@ -356,17 +453,17 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT sa = vfma(-al, q, s);
                         Pv[row] = p; U[row] = u; W[row] = w; Tv[row] = t; Z[row] = z;
                         Y[row] = yn; X[row] = x; R[row] = rn; L[row] = q; G[row] = gp; sNxt[row] = sa;
-                        dacc(pv[SB], yn, yn);
-                        dacc(pv[SE], yn, rn);
-                        dacc(pv[SF], rs, rn);
-                        dacc(pv[SH], rs, t);
-                        dacc(pv[SR], rn, rn);
+                        xa_acc(xv[SB], yn, yn);
+                        xa_acc(xv[SE], yn, rn);
+                        xa_acc(xv[SF], rs, rn);
+                        xa_acc(xv[SH], rs, t);
+                        xa_acc(xv[SR], rn, rn);
                     }
                 }
-                flush(nxt, pv, (1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR));
+                flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
                 // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
-                zero10(pv);
+                xa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT Aw = spmv(W, tile);
                     const int64_t row = tile * 32 + lane;
@@ -377,13 +474,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT s = sa - g;
                         L[row] = l; G[row] = g; sNxt[row] = s;
                         const VT y = Y[row], r = R[row], rs = RS[row];
-                        dacc(pv[SA], s, s);
-                        dacc(pv[SC], s, y);
-                        dacc(pv[SD], s, r);
-                        dacc(pv[SG], rs, s);
+                        xa_acc(xv[SA], s, s);
+                        xa_acc(xv[SC], s, y);
+                        xa_acc(xv[SD], s, r);
+                        xa_acc(xv[SG], rs, s);
                     }
                 }
-                flush(nxt, pv, (1u << SA) | (1u << SC) | (1u << SD) | (1u << SG));
+                flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
             } else {
@@ -416,7 +513,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 if (!grp.sync(&s_flag)) return;
                 // r_{i+1} = b - A x_{i+1}; l_i = A t_i; g_{i+1} = A y_{i+1}
-                zero10(pv);
+                xa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT ax = spmv(X, tile);
                     const VT at = spmv(Tv, tile);
@@ -426,30 +523,30 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT rn = Bin[row] - ax;
                         const VT y = Y[row], t = Tv[row], rs = RS[row];
                         R[row] = rn; L[row] = at; G[row] = ay;
-                        dacc(pv[SB], y, y);
-                        dacc(pv[SE], y, rn);
-                        dacc(pv[SF], rs, rn);
-                        dacc(pv[SH], rs, t);
-                        dacc(pv[SR], rn, rn);
+                        xa_acc(xv[SB], y, y);
+                        xa_acc(xv[SE], y, rn);
+                        xa_acc(xv[SF], rs, rn);
+                        xa_acc(xv[SH], rs, t);
+                        xa_acc(xv[SR], rn, rn);
                     }
                 }
-                flush(nxt, pv, (1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR));
+                flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
                 // s_{i+1} = A r_{i+1}
-                zero10(pv);
+                xa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT s = spmv(R, tile);
                     const int64_t row = tile * 32 + lane;
                     if (row < n) {
                         sNxt[row] = s;
                         const VT y = Y[row], r = R[row], rs = RS[row];
-                        dacc(pv[SA], s, s);
-                        dacc(pv[SC], s, y);
-                        dacc(pv[SD], s, r);
-                        dacc(pv[SG], rs, s);
+                        xa_acc(xv[SA], s, s);
+                        xa_acc(xv[SC], s, y);
+                        xa_acc(xv[SD], s, r);
+                        xa_acc(xv[SG], rs, s);
                     }
                 }
-                flush(nxt, pv, (1u << SA) | (1u << SC) | (1u << SD) | (1u << SG));
+                flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
                 ++rr_steps;
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
@@ -509,19 +606,22 @@ int max_grid_one(int* grid) {
     return (int)e;
 }
 
-// Dispatch over layout and lanes-per-row for one (VT, MT) pair.
-template <class VT, class MT>
+// Dispatch over layout and lanes-per-row for one (VT, MT) pair; each
+// translation unit instantiates one subset (SUBSET 0: SELL and CSR with 1 lane
+// per row, SUBSET 1: CSR with 4, 8 or 32 lanes per row).
+template <class VT, class MT, int SUBSET>
 int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
 #define BCS_CASE(LAY, TT)                                                              \
     return P ? launch_one<VT, MT, LAY, TT>(*P, grid, st) : max_grid_one<VT, MT, LAY, TT>(max_grid)
-    if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1); }
-    switch (tpr) {
-        case 1: BCS_CASE(LAY_CSR, 1);
-        case 2: BCS_CASE(LAY_CSR, 2);
-        case 4: BCS_CASE(LAY_CSR, 4);
-        case 8: BCS_CASE(LAY_CSR, 8);
-        case 16: BCS_CASE(LAY_CSR, 16);
-        default: BCS_CASE(LAY_CSR, 32);
+    if constexpr (SUBSET == 0) {
+        if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1); }
+        BCS_CASE(LAY_CSR, 1);
+    } else {
+        switch (tpr) {
+            case 4: BCS_CASE(LAY_CSR, 4);
+            case 8: BCS_CASE(LAY_CSR, 8);
+            default: BCS_CASE(LAY_CSR, 32);
+        }
     }
 #undef BCS_CASE
 }
@@ -579,7 +679,7 @@ __global__ void __launch_bounds__(kBlock) batched_kernel(const __grid_constant__
             sP = B.sys[B.order[k]];
             char* base = B.ws + (size_t)cid * B.ws_group_bytes;
             for (int v = 0; v < NVEC; ++v) sP.vec[v] = base + (size_t)v * B.vec_bytes;
-            sP.partials = B.partials + (size_t)cid * 2 * B.csize * NSLOT;
+            sP.partials = B.partials + (size_t)cid * 2 * B.csize * NSLOT * kRec;
         }
         __syncthreads();
         solve_body<VT, MT, LAY_CSR, T>(sP, grp);
@@ -599,13 +699,7 @@ int dispatch_batched(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void (*fn)(BatchArgs) = nullptr;
-    switch (tpr) {
-        case 1: fn = batched_kernel<VT, MT, 1>; break;
-        case 4: fn = batched_kernel<VT, MT, 4>; break;
-        case 8: fn = batched_kernel<VT, MT, 8>; break;
-        default: fn = batched_kernel<VT, MT, 32>; break;
-    }
+    void (*fn)(BatchArgs) = (tpr == 1) ? batched_kernel<VT, MT, 1> : batched_kernel<VT, MT, 8>;
     cudaError_t e = cudaSuccess;
     if (B->csize > 8) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;

@@ -1,0 +1,8 @@
+// Persistent solver kernels, float vectors and float matrix values (instantiation subset 0).
+#include "solver.cuh"
+
+namespace bcs {
+int dispatch_f32_0(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
+    return dispatch<float, float, 0>(P, layout, tpr, grid, st, max_grid);
+}
+}  // namespace bcs
