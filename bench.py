@@ -51,6 +51,7 @@ def args_parse():
     ap.add_argument("--kind", default="p-BiCGSafe")
     ap.add_argument("--tpr", type=int, default=0, help="CSR lanes per row (0 = library default)")
     ap.add_argument("--layout", default="csr")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / mixed side measurements")
     ap.add_argument("--cpu-iters", type=int, default=30, help="oracle iterations in the CPU sample")
     ap.add_argument("--size", type=int, default=128, help="grid side k of the k^3 system (128 = the benchmark)")
@@ -204,7 +205,7 @@ def main():
     A, b = make_workload(a.size)
     n, nnz = A.n, A.nnz
     layouts = bcs.LAYOUT_CSR | (bcs.LAYOUT_SELL if a.layout == "sell" else 0)
-    M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32)
+    M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32 | bcs.STORE_BF16)
     stream = torch.cuda.current_stream()
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
@@ -245,7 +246,7 @@ def main():
         return total_ms, per, results
 
     with Clocks(local) as ck:
-        total_ms, per, results = run(a.kind, "fp64", a.steps, a.warmup)
+        total_ms, per, results = run(a.kind, a.precision, a.steps, a.warmup)
     clocks = ck.summary()
     if dist:
         t = torch.tensor([total_ms], device="cuda")

@@ -165,6 +165,12 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (o.ctas_per_sm > 0) grid = std::min(grid, o.ctas_per_sm * sms);
     if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (ntiles + kWarps - 1) / kWarps));
+    // each lane's exact inner-product partial holds one product per tile: keep
+    // the tiles per warp below 2^16 so that it cannot overflow its 128 bits
+    if ((ntiles + (int64_t)grid * kWarps - 1) / ((int64_t)grid * kWarps) >= (1 << 16)) {
+        delete s;
+        return BCS_ERR_ARG;
+    }
     s->grid = grid;
     auto alloc = [&](void** p, size_t bytes) {
         if (rc) return;
@@ -342,6 +348,7 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
     double sum_avg = 0.0;
     for (int k = 0; k < nsys; ++k) {
         if (!A[k] || !(A[k]->layouts & BCS_LAYOUT_CSR)) return BCS_ERR_ARG;
+        if ((A[k]->n + 31) / 32 >= (int64_t)(1 << 16) * kWarps) return BCS_ERR_ARG;  // see bcs_solver_create
         if (A[k]->n > 0 && (!b[k] || !x[k])) return BCS_ERR_ARG;
         rc = precision_types(A[k], o.precision, &vt_f32, &valtype);
         if (rc) return rc;

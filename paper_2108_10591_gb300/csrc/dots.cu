@@ -13,10 +13,14 @@ namespace {
 template <class VT>
 __global__ void __launch_bounds__(kBlock) k_dot_partial(int64_t n, const VT* x, const VT* y, unsigned long long* recs) {
     __shared__ XStage s_x;
-    XAcc a[10];
-    xa_init10(a);
-    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
-        xa_acc(a[0], x[i], y[i]);
+    WAcc a[10];
+    wa_init10(a);
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = blockIdx.x * (int64_t)kBlock + (threadIdx.x - lane); b < n; b += (int64_t)gridDim.x * kBlock) {
+        const int64_t i = b + lane;
+        const bool ok = i < n;
+        wa_acc(a[0], ok ? x[i] : VT(0), ok ? y[i] : VT(0), ok);
+    }
     flush_partials<1u>(a, s_x, recs + (size_t)blockIdx.x * NSLOT * kRec);
 }
 

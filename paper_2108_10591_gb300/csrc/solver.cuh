@@ -39,72 +39,63 @@
 namespace bcs {
 
 // ---- exact inner-product partials ------------------------------------------------------
-// Per-CTA records: NSLOT slots x (anchor, hi, lo) as three 64-bit words.
-constexpr int kRec = 3;
+// Per-CTA records: NSLOT slots x (anchor, w2, w1, w0) as four 64-bit words.
+constexpr int kRec = 4;
 
-__device__ __forceinline__ void xa_init10(XAcc (&a)[10]) {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) xa_init(a[k]);
-}
 
-// Shared scratch of the block-level merges: every thread stages up to kStage
-// accumulators; the merge then loops over slots at run time (one copy of the
-// merge code instead of one per slot and call site).
-constexpr int kStage = 5;
+// Shared scratch of the block-level reductions: one exact accumulator per
+// slot and warp.
 struct XStage {
-    XAcc v[kStage][kBlock];
-    XAcc w[kStage][kWarps];
+    XAcc w[10][kWarps];
 };
 
-// Merge the staged accumulators v[0..ns) over the block: warp butterflies, then
-// one more over the per-warp results.  Result of slot j in v[j][0].
-__device__ __forceinline__ void xa_block_merge(XStage& st, int ns) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    __syncthreads();
-#pragma unroll 1
-    for (int j = 0; j < ns; ++j) {
-        XAcc a = st.v[j][t];
-        xa_warp_merge(a);
-        if (lane == 0) st.w[j][warp] = a;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll 1
-        for (int j = 0; j < ns; ++j) {
-            XAcc a;
-            if (lane < kWarps) a = st.w[j][lane]; else xa_init(a);
-            xa_warp_merge(a);
-            if (lane == 0) st.v[j][0] = a;
+__device__ __forceinline__ void wa_init10(WAcc (&a)[10]) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) wa_init(a[k]);
+}
+
+__device__ __forceinline__ void store_rec(unsigned long long* rec, int k, const XAcc& t) {
+    rec[k * kRec + 0] = (unsigned long long)(long long)t.e;
+    rec[k * kRec + 1] = t.w2;
+    rec[k * kRec + 2] = t.w1;
+    rec[k * kRec + 3] = t.w0;
+}
+__device__ __forceinline__ XAcc load_rec(const unsigned long long* r) {
+    XAcc t;
+    t.e = (int)(long long)r[0];
+    t.w2 = r[1];
+    t.w1 = r[2];
+    t.w0 = r[3];
+    return t;
+}
+
+// Sum the CTA's warp accumulators of the slots in MASK exactly and store them
+// as the CTA's record; slots in ZMASK are recorded as empty (zero).
+template <unsigned MASK, unsigned ZMASK = 0u>
+__device__ __forceinline__ void flush_partials(WAcc (&a)[10], XStage& st, unsigned long long* rec) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        if ((MASK >> k) & 1u) {
+            const XAcc t = wa_warp_total(a[k]);
+            if (lane == 0) st.w[k][warp] = t;
         }
     }
     __syncthreads();
-}
-
-// Merge the CTA's accumulators of the slots in MASK (at most kStage) and store
-// them as the CTA's record; slots in ZMASK are recorded as empty (zero).
-template <unsigned MASK, unsigned ZMASK = 0u>
-__device__ __forceinline__ void flush_partials(XAcc (&a)[10], XStage& st, unsigned long long* rec) {
-    static_assert(__builtin_popcount(MASK) <= kStage, "too many slots");
-    {
-        int j = 0;
-#pragma unroll
-        for (int k = 0; k < 10; ++k)
-            if ((MASK >> k) & 1u) st.v[j++][threadIdx.x] = a[k];
-    }
-    xa_block_merge(st, __builtin_popcount(MASK));
-    if (threadIdx.x == 0) {
-        int j = 0;
+    if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < 10; ++k) {
             if ((MASK >> k) & 1u) {
-                const XAcc& t = st.v[j++][0];
-                rec[k * kRec + 0] = (unsigned long long)(long long)t.e;
-                rec[k * kRec + 1] = t.hi;
-                rec[k * kRec + 2] = t.lo;
+                XAcc t;
+                if (lane < kWarps) t = st.w[k][lane]; else xa_init(t);
+                t = xa_warp_aligned_sum(t);
+                if (lane == 0) store_rec(rec, k, t);
             } else if ((ZMASK >> k) & 1u) {
-                rec[k * kRec + 0] = (unsigned long long)(long long)kXaEmpty;
-                rec[k * kRec + 1] = 0;
-                rec[k * kRec + 2] = 0;
+                if (lane == 0) {
+                    XAcc z;
+                    xa_init(z);
+                    store_rec(rec, k, z);
+                }
             }
         }
     }
@@ -117,32 +108,35 @@ __device__ __forceinline__ void prefetch_partials(const unsigned long long* base
         const char* r = (const char*)(base + (size_t)c * NSLOT * kRec);
         asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
         asm volatile("prefetch.global.L1 [%0];" ::"l"(r + 128));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(r + 256));
     }
 }
 
-// Sum every CTA's record (the same order in every CTA, so all CTAs obtain the
-// same values) and round each slot once: out[k] = correctly rounded slot k.
+// Sum every CTA's record exactly (all CTAs obtain the same values) and round
+// each slot once: out[k] = correctly rounded slot k.
 __device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage& st, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 1
-    for (int k0 = 0; k0 < 10; k0 += kStage) {
-#pragma unroll 1
-        for (int j = 0; j < kStage; ++j) {
-            XAcc a;
-            xa_init(a);
-            for (int c = threadIdx.x; c < nblk; c += kBlock) {
-                const unsigned long long* r = base + (size_t)c * NSLOT * kRec + (k0 + j) * kRec;
-                XAcc t;
-                t.e = (int)(long long)r[0];
-                t.hi = r[1];
-                t.lo = r[2];
-                xa_merge(a, t);
-            }
-            st.v[j][threadIdx.x] = a;
+    for (int k = 0; k < 10; ++k) {
+        XAcc a;
+        xa_init(a);
+        for (int c = threadIdx.x; c < nblk; c += kBlock) {
+            xa_merge(a, load_rec(base + (size_t)c * NSLOT * kRec + k * kRec));
         }
-        xa_block_merge(st, kStage);
-        if (threadIdx.x < kStage) out[k0 + threadIdx.x] = xa_round(st.v[threadIdx.x][0]);
-        __syncthreads();
+        a = xa_warp_aligned_sum(a);
+        if (lane == 0) st.w[k][warp] = a;
     }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll 1
+        for (int k = 0; k < 10; ++k) {
+            XAcc t;
+            if (lane < kWarps) t = st.w[k][lane]; else xa_init(t);
+            t = xa_warp_aligned_sum(t);
+            if (lane == 0) out[k] = xa_round(t);
+        }
+    }
+    __syncthreads();
 }
 
 // A set of CTAs that solve one system together: the whole cooperative grid
@@ -236,14 +230,17 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     for (;;) {
         // ---------------- true residual r = b - A x (FP64) and (re)initialisation ----------
         {
-            XAcc xv[10];
-            xa_init10(xv);
+            WAcc xv[10];
+            wa_init10(xv);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const double ax = spmv64(P.x64, tile);
                 const int64_t row = tile * 32 + lane;
+                double qa_ST = double(0), qb_ST = double(0);
+                VT qa_SF = VT(0), qb_SF = VT(0);
                 if (row < n) {
                     const double r64 = P.b64[row] - ax;
-                    xa_fma64(xv[ST], r64, r64);
+                    qa_ST = r64;
+                    qb_ST = r64;
                     const VT rv = (VT)r64;
                     R[row] = rv;
                     RS[row] = rv;
@@ -253,8 +250,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     }
                     Y[row] = VT(0); Tv[row] = VT(0); Pv[row] = VT(0); U[row] = VT(0);
                     Z[row] = VT(0); W[row] = VT(0); L[row] = VT(0); G[row] = VT(0);
-                    xa_acc(xv[SF], rv, rv);
+                    qa_SF = rv;
+                    qb_SF = rv;
                 }
+                wa_acc(xv[ST], qa_ST, qb_ST, row < n);
+                wa_acc(xv[SF], qa_SF, qb_SF, row < n);
             }
             xv[SR] = xv[SF];
             flush_partials<(1u << ST) | (1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(
@@ -280,18 +280,27 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 
         // ---------------- pipelined set-up: s_0 = A r_0 and the i = 0 products --------------
         if (kind != BCS_SSBICGSAFE2) {
-            XAcc xv[10];
-            xa_init10(xv);
+            WAcc xv[10];
+            wa_init10(xv);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const VT sv = spmv(R, tile);
                 const int64_t row = tile * 32 + lane;
+                VT qa_SA = VT(0), qb_SA = VT(0);
+                VT qa_SD = VT(0), qb_SD = VT(0);
+                VT qa_SG = VT(0), qb_SG = VT(0);
                 if (row < n) {
                     sCur[row] = sv;
                     const VT rv = R[row], rsv = RS[row];
-                    xa_acc(xv[SA], sv, sv);
-                    xa_acc(xv[SD], sv, rv);
-                    xa_acc(xv[SG], rsv, sv);
+                    qa_SA = sv;
+                    qb_SA = sv;
+                    qa_SD = sv;
+                    qb_SD = rv;
+                    qa_SG = rsv;
+                    qb_SG = sv;
                 }
+                wa_acc(xv[SA], qa_SA, qb_SA, row < n);
+                wa_acc(xv[SD], qa_SD, qb_SD, row < n);
+                wa_acc(xv[SG], qa_SG, qb_SG, row < n);
             }
             flush_partials<(1u << SA) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(0));
             if (!grp.sync(&s_flag)) return;
@@ -302,22 +311,34 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         for (;; ++i) {
             const int cur = i & 1, nxt = cur ^ 1;
             const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
-            XAcc xv[10];
+            WAcc xv[10];
             VT as_first = VT(0);
             if (kind == BCS_SSBICGSAFE2) {
                 // phase A: s_i = A r_i and the products involving s_i
-                xa_init10(xv);
+                wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT sv = spmv(R, tile);
                     const int64_t row = tile * 32 + lane;
+                    VT qa_SA = VT(0), qb_SA = VT(0);
+                    VT qa_SC = VT(0), qb_SC = VT(0);
+                    VT qa_SD = VT(0), qb_SD = VT(0);
+                    VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
                         sCur[row] = sv;
                         const VT yv = Y[row], rv = R[row], rsv = RS[row];
-                        xa_acc(xv[SA], sv, sv);
-                        xa_acc(xv[SC], sv, yv);
-                        xa_acc(xv[SD], sv, rv);
-                        xa_acc(xv[SG], rsv, sv);
+                        qa_SA = sv;
+                        qb_SA = sv;
+                        qa_SC = sv;
+                        qb_SC = yv;
+                        qa_SD = sv;
+                        qb_SD = rv;
+                        qa_SG = rsv;
+                        qb_SG = sv;
                     }
+                    wa_acc(xv[SA], qa_SA, qb_SA, row < n);
+                    wa_acc(xv[SC], qa_SC, qb_SC, row < n);
+                    wa_acc(xv[SD], qa_SD, qb_SD, row < n);
+                    wa_acc(xv[SG], qa_SG, qb_SG, row < n);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(cur));
                 if (!grp.sync(&s_flag)) return;
@@ -407,10 +428,15 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 if (!grp.sync(&s_flag)) return;
                 // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
-                xa_init10(xv);
+                wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT w = spmv(U, tile);
                     const int64_t row = tile * 32 + lane;
+                    VT qa_SB = VT(0), qb_SB = VT(0);
+                    VT qa_SE = VT(0), qb_SE = VT(0);
+                    VT qa_SF = VT(0), qb_SF = VT(0);
+                    VT qa_SH = VT(0), qb_SH = VT(0);
+                    VT qa_SR = VT(0), qb_SR = VT(0);
                     if (row < n) {
                         const VT o = O[row], r = R[row], u = U[row], s = sCur[row], y = Y[row], p = Pv[row], rs = RS[row];
                         VT z = Z[row], x = X[row];
@@ -420,21 +446,36 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         x = vfma(al, p, x) + z;
                         const VT rn = vfma(-al, o, r) - yn;
                         Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x; R[row] = rn;
-                        xa_acc(xv[SB], yn, yn);
-                        xa_acc(xv[SE], yn, rn);
-                        xa_acc(xv[SF], rs, rn);
-                        xa_acc(xv[SH], rs, t);
-                        xa_acc(xv[SR], rn, rn);
+                        qa_SB = yn;
+                        qb_SB = yn;
+                        qa_SE = yn;
+                        qb_SE = rn;
+                        qa_SF = rs;
+                        qb_SF = rn;
+                        qa_SH = rs;
+                        qb_SH = t;
+                        qa_SR = rn;
+                        qb_SR = rn;
                     }
+                    wa_acc(xv[SB], qa_SB, qb_SB, row < n);
+                    wa_acc(xv[SE], qa_SE, qb_SE, row < n);
+                    wa_acc(xv[SF], qa_SF, qb_SF, row < n);
+                    wa_acc(xv[SH], qa_SH, qb_SH, row < n);
+                    wa_acc(xv[SR], qa_SR, qb_SR, row < n);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
             } else if (!rr_step) {
                 // phase A (continued): fused recurrences of Alg. 4
-                xa_init10(xv);
+                wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT As = (tile == gwarp) ? as_first : spmv(sCur, tile);
                     const int64_t row = tile * 32 + lane;
+                    VT qa_SB = VT(0), qb_SB = VT(0);
+                    VT qa_SE = VT(0), qb_SE = VT(0);
+                    VT qa_SF = VT(0), qb_SF = VT(0);
+                    VT qa_SH = VT(0), qb_SH = VT(0);
+                    VT qa_SR = VT(0), qb_SR = VT(0);
                     if (row < n) {
                         const VT r = R[row], s = sCur[row], rs = RS[row];
                         VT p = Pv[row], u = U[row], t = Tv[row], l = L[row], y = Y[row], g = G[row];
@@ -453,20 +494,34 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT sa = vfma(-al, q, s);
                         Pv[row] = p; U[row] = u; W[row] = w; Tv[row] = t; Z[row] = z;
                         Y[row] = yn; X[row] = x; R[row] = rn; L[row] = q; G[row] = gp; sNxt[row] = sa;
-                        xa_acc(xv[SB], yn, yn);
-                        xa_acc(xv[SE], yn, rn);
-                        xa_acc(xv[SF], rs, rn);
-                        xa_acc(xv[SH], rs, t);
-                        xa_acc(xv[SR], rn, rn);
+                        qa_SB = yn;
+                        qb_SB = yn;
+                        qa_SE = yn;
+                        qb_SE = rn;
+                        qa_SF = rs;
+                        qb_SF = rn;
+                        qa_SH = rs;
+                        qb_SH = t;
+                        qa_SR = rn;
+                        qb_SR = rn;
                     }
+                    wa_acc(xv[SB], qa_SB, qb_SB, row < n);
+                    wa_acc(xv[SE], qa_SE, qb_SE, row < n);
+                    wa_acc(xv[SF], qa_SF, qb_SF, row < n);
+                    wa_acc(xv[SH], qa_SH, qb_SH, row < n);
+                    wa_acc(xv[SR], qa_SR, qb_SR, row < n);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
                 // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
-                xa_init10(xv);
+                wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT Aw = spmv(W, tile);
                     const int64_t row = tile * 32 + lane;
+                    VT qa_SA = VT(0), qb_SA = VT(0);
+                    VT qa_SC = VT(0), qb_SC = VT(0);
+                    VT qa_SD = VT(0), qb_SD = VT(0);
+                    VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
                         const VT q = L[row], gp = G[row], sa = sNxt[row];
                         const VT l = q - Aw;
@@ -474,11 +529,19 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT s = sa - g;
                         L[row] = l; G[row] = g; sNxt[row] = s;
                         const VT y = Y[row], r = R[row], rs = RS[row];
-                        xa_acc(xv[SA], s, s);
-                        xa_acc(xv[SC], s, y);
-                        xa_acc(xv[SD], s, r);
-                        xa_acc(xv[SG], rs, s);
+                        qa_SA = s;
+                        qb_SA = s;
+                        qa_SC = s;
+                        qb_SC = y;
+                        qa_SD = s;
+                        qb_SD = r;
+                        qa_SG = rs;
+                        qb_SG = s;
                     }
+                    wa_acc(xv[SA], qa_SA, qb_SA, row < n);
+                    wa_acc(xv[SC], qa_SC, qb_SC, row < n);
+                    wa_acc(xv[SD], qa_SD, qb_SD, row < n);
+                    wa_acc(xv[SG], qa_SG, qb_SG, row < n);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
@@ -513,38 +576,65 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 if (!grp.sync(&s_flag)) return;
                 // r_{i+1} = b - A x_{i+1}; l_i = A t_i; g_{i+1} = A y_{i+1}
-                xa_init10(xv);
+                wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT ax = spmv(X, tile);
                     const VT at = spmv(Tv, tile);
                     const VT ay = spmv(Y, tile);
                     const int64_t row = tile * 32 + lane;
+                    VT qa_SB = VT(0), qb_SB = VT(0);
+                    VT qa_SE = VT(0), qb_SE = VT(0);
+                    VT qa_SF = VT(0), qb_SF = VT(0);
+                    VT qa_SH = VT(0), qb_SH = VT(0);
+                    VT qa_SR = VT(0), qb_SR = VT(0);
                     if (row < n) {
                         const VT rn = Bin[row] - ax;
                         const VT y = Y[row], t = Tv[row], rs = RS[row];
                         R[row] = rn; L[row] = at; G[row] = ay;
-                        xa_acc(xv[SB], y, y);
-                        xa_acc(xv[SE], y, rn);
-                        xa_acc(xv[SF], rs, rn);
-                        xa_acc(xv[SH], rs, t);
-                        xa_acc(xv[SR], rn, rn);
+                        qa_SB = y;
+                        qb_SB = y;
+                        qa_SE = y;
+                        qb_SE = rn;
+                        qa_SF = rs;
+                        qb_SF = rn;
+                        qa_SH = rs;
+                        qb_SH = t;
+                        qa_SR = rn;
+                        qb_SR = rn;
                     }
+                    wa_acc(xv[SB], qa_SB, qb_SB, row < n);
+                    wa_acc(xv[SE], qa_SE, qb_SE, row < n);
+                    wa_acc(xv[SF], qa_SF, qb_SF, row < n);
+                    wa_acc(xv[SH], qa_SH, qb_SH, row < n);
+                    wa_acc(xv[SR], qa_SR, qb_SR, row < n);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
                 // s_{i+1} = A r_{i+1}
-                xa_init10(xv);
+                wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT s = spmv(R, tile);
                     const int64_t row = tile * 32 + lane;
+                    VT qa_SA = VT(0), qb_SA = VT(0);
+                    VT qa_SC = VT(0), qb_SC = VT(0);
+                    VT qa_SD = VT(0), qb_SD = VT(0);
+                    VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
                         sNxt[row] = s;
                         const VT y = Y[row], r = R[row], rs = RS[row];
-                        xa_acc(xv[SA], s, s);
-                        xa_acc(xv[SC], s, y);
-                        xa_acc(xv[SD], s, r);
-                        xa_acc(xv[SG], rs, s);
+                        qa_SA = s;
+                        qb_SA = s;
+                        qa_SC = s;
+                        qb_SC = y;
+                        qa_SD = s;
+                        qb_SD = r;
+                        qa_SG = rs;
+                        qb_SG = s;
                     }
+                    wa_acc(xv[SA], qa_SA, qb_SA, row < n);
+                    wa_acc(xv[SC], qa_SC, qb_SC, row < n);
+                    wa_acc(xv[SD], qa_SD, qb_SD, row < n);
+                    wa_acc(xv[SG], qa_SG, qb_SG, row < n);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) return;
@@ -583,7 +673,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 }
 
 template <class VT, class MT, int LAYOUT, int T>
-__global__ void __launch_bounds__(kBlock) solve_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(kBlock, 3) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
     solve_body<VT, MT, LAYOUT, T>(P, grp);
 }

@@ -23,9 +23,13 @@ constexpr int kXaTop = 110;              // anchor headroom: terms end at or bel
 constexpr int kXaEmpty = -(1 << 29);     // e of an accumulator with no terms
 constexpr int kXaNaN = (1 << 29);        // e of an accumulator that saw a NaN/Inf operand
 
+// Merged partial sums (warp totals, CTA records, grid totals): 192-bit two's
+// complement, value = (w2:w1:w0) * 2^e.  The per-lane partials of the solver
+// use the cheaper 128-bit WAcc below; 192 bits leave room for every merge
+// (at most 2^19 products per lane, 2^26 lanes) without dropping bits.
 struct XAcc {
     int e;
-    unsigned long long hi, lo;  // 128-bit two's complement
+    unsigned long long w2, w1, w0;
 };
 
 __host__ __device__ __forceinline__ int xa_clz64(unsigned long long v) {
@@ -45,25 +49,10 @@ __host__ __device__ __forceinline__ unsigned long long xa_mulhi64(unsigned long 
 
 __host__ __device__ __forceinline__ void xa_init(XAcc& a) {
     a.e = kXaEmpty;
-    a.hi = 0;
-    a.lo = 0;
+    a.w2 = a.w1 = a.w0 = 0;
 }
 
-// arithmetic shift right of (hi, lo) by d >= 0
-__host__ __device__ __forceinline__ void xa_sra(unsigned long long& hi, unsigned long long& lo, int d) {
-    if (d <= 0) return;
-    const long long sh = (long long)hi;
-    if (d >= 128) {
-        hi = lo = (unsigned long long)(sh >> 63);
-    } else if (d >= 64) {
-        lo = (unsigned long long)(sh >> (d - 64));
-        hi = (unsigned long long)(sh >> 63);
-    } else {
-        lo = (lo >> d) | (hi << (64 - d));
-        hi = (unsigned long long)(sh >> d);
-    }
-}
-
+// 128-bit helpers (per-lane partials)
 __host__ __device__ __forceinline__ void xa_add128(unsigned long long& hi, unsigned long long& lo,
                                                    unsigned long long th, unsigned long long tl) {
     const unsigned long long l = lo + tl;
@@ -71,111 +60,49 @@ __host__ __device__ __forceinline__ void xa_add128(unsigned long long& hi, unsig
     lo = l;
 }
 
-// Keep |w| < 2^124 so that adding two accumulators never overflows.
+// 192-bit helpers: arithmetic shift right by d >= 0 (branch-free selects) and add.
+__host__ __device__ __forceinline__ void xa_sar192(XAcc& a, int d) {
+    const long long sg = (long long)a.w2 >> 63;
+    unsigned long long w0 = a.w0, w1 = a.w1, w2 = a.w2;
+    const int q = d >= 192 ? 3 : d / 64;   // whole words
+    const int r = d >= 192 ? 0 : d % 64;   // bits
+    // word shift
+    const unsigned long long s2 = (unsigned long long)sg;
+    unsigned long long t0 = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : s2;
+    unsigned long long t1 = q == 0 ? w1 : q == 1 ? w2 : s2;
+    unsigned long long t2 = q == 0 ? w2 : s2;
+    // bit shift
+    if (r) {
+        t0 = (t0 >> r) | (t1 << (64 - r));
+        t1 = (t1 >> r) | (t2 << (64 - r));
+        t2 = (unsigned long long)((long long)t2 >> r);
+    }
+    a.w0 = t0;
+    a.w1 = t1;
+    a.w2 = t2;
+}
+__host__ __device__ __forceinline__ void xa_add192(XAcc& a, unsigned long long b2, unsigned long long b1,
+                                                   unsigned long long b0) {
+    const unsigned long long s0 = a.w0 + b0;
+    const unsigned long long c0 = s0 < a.w0 ? 1ull : 0ull;
+    const unsigned long long s1a = a.w1 + b1;
+    const unsigned long long c1a = s1a < a.w1 ? 1ull : 0ull;
+    const unsigned long long s1 = s1a + c0;
+    const unsigned long long c1 = c1a + (s1 < s1a ? 1ull : 0ull);
+    a.w0 = s0;
+    a.w1 = s1;
+    a.w2 = a.w2 + b2 + c1;
+}
+// keep |w| < 2^188 (merges add at most a few bits before the next normalisation)
 __host__ __device__ __forceinline__ void xa_norm(XAcc& a) {
-    const long long t = (long long)a.hi >> 60;  // 0 or -1 when |w| < 2^124
+    const long long t = (long long)a.w2 >> 60;
     if (t != 0 && t != -1) {
-        xa_sra(a.hi, a.lo, 4);
-        a.e += 4;
+        xa_sar192(a, 8);
+        a.e += 8;
     }
 }
 
-// Add the term (ph:pl) * 2^e (unsigned magnitude, 1 <= ph:pl < 2^107), negated if neg.
-__host__ __device__ __forceinline__ void xa_add_term(XAcc& a, unsigned long long ph, unsigned long long pl, int e,
-                                                     bool neg) {
-    const int len = ph ? 128 - xa_clz64(ph) : 64 - xa_clz64(pl);
-    const int top = e + len;
-    if (a.e == kXaNaN) return;
-    if (a.e == kXaEmpty) {
-        a.e = top - kXaTop;
-    } else if (top > a.e + kXaTop) {
-        const int d = top - kXaTop - a.e;
-        xa_sra(a.hi, a.lo, d);
-        a.e += d;
-    }
-    int s = e - a.e;  // <= kXaTop - len
-    unsigned long long th, tl;
-    if (s >= 0) {
-        if (s >= 64) {
-            th = pl << (s - 64);
-            tl = 0;
-        } else if (s > 0) {
-            th = (ph << s) | (pl >> (64 - s));
-            tl = pl << s;
-        } else {
-            th = ph;
-            tl = pl;
-        }
-    } else {
-        s = -s;
-        if (s >= 128) {
-            th = tl = 0;
-        } else if (s >= 64) {
-            tl = ph >> (s - 64);
-            th = 0;
-        } else {
-            tl = (pl >> s) | (ph << (64 - s));
-            th = ph >> s;
-        }
-    }
-    if (neg) {
-        tl = ~tl + 1ull;
-        th = ~th + (tl == 0 ? 1ull : 0ull);
-    }
-    xa_add128(a.hi, a.lo, th, tl);
-    xa_norm(a);
-}
-
-// x * y for FP64 operands.
-__host__ __device__ __forceinline__ void xa_fma64(XAcc& a, double x, double y) {
-#ifdef __CUDA_ARCH__
-    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long by = (unsigned long long)__double_as_longlong(y);
-#else
-    unsigned long long bx, by;
-    __builtin_memcpy(&bx, &x, 8);
-    __builtin_memcpy(&by, &y, 8);
-#endif
-    const int Ex = (int)((bx >> 52) & 0x7FF), Ey = (int)((by >> 52) & 0x7FF);
-    if (Ex == 0x7FF || Ey == 0x7FF) {
-        a.e = kXaNaN;
-        return;
-    }
-    unsigned long long mx = bx & 0xFFFFFFFFFFFFFull, my = by & 0xFFFFFFFFFFFFFull;
-    if (Ex) mx |= 1ull << 52;
-    if (Ey) my |= 1ull << 52;
-    if (mx == 0 || my == 0) return;
-    const int e = (Ex ? Ex - 1075 : -1074) + (Ey ? Ey - 1075 : -1074);
-    xa_add_term(a, xa_mulhi64(mx, my), mx * my, e, ((bx ^ by) >> 63) != 0);
-}
-
-// x * y for FP32 operands (the product is at most 48 bits).
-__host__ __device__ __forceinline__ void xa_fma32(XAcc& a, float x, float y) {
-#ifdef __CUDA_ARCH__
-    const unsigned bx = __float_as_uint(x), by = __float_as_uint(y);
-#else
-    unsigned bx, by;
-    __builtin_memcpy(&bx, &x, 4);
-    __builtin_memcpy(&by, &y, 4);
-#endif
-    const int Ex = (int)((bx >> 23) & 0xFF), Ey = (int)((by >> 23) & 0xFF);
-    if (Ex == 0xFF || Ey == 0xFF) {
-        a.e = kXaNaN;
-        return;
-    }
-    unsigned mx = bx & 0x7FFFFFu, my = by & 0x7FFFFFu;
-    if (Ex) mx |= 1u << 23;
-    if (Ey) my |= 1u << 23;
-    if (mx == 0 || my == 0) return;
-    const int e = (Ex ? Ex - 150 : -149) + (Ey ? Ey - 150 : -149);
-    xa_add_term(a, 0ull, (unsigned long long)mx * my, e, ((bx ^ by) >> 31) != 0);
-}
-
-__host__ __device__ __forceinline__ void xa_acc(XAcc& a, double x, double y) { xa_fma64(a, x, y); }
-__host__ __device__ __forceinline__ void xa_acc(XAcc& a, float x, float y) { xa_fma32(a, x, y); }
-
-// a += b (both exact accumulators); symmetric, so both partners of a
-// butterfly step obtain bitwise the same result.
+// a += b for two merged partials (general anchors); symmetric.
 __host__ __device__ __forceinline__ void xa_merge(XAcc& a, const XAcc& b) {
     if (a.e == kXaNaN || b.e == kXaNaN) {
         a.e = kXaNaN;
@@ -187,14 +114,13 @@ __host__ __device__ __forceinline__ void xa_merge(XAcc& a, const XAcc& b) {
         return;
     }
     const int E = a.e > b.e ? a.e : b.e;
-    unsigned long long ah = a.hi, al = a.lo, bh = b.hi, bl = b.lo;
-    xa_sra(ah, al, E - a.e);
-    xa_sra(bh, bl, E - b.e);
-    xa_add128(ah, al, bh, bl);
-    a.hi = ah;
-    a.lo = al;
-    a.e = E;
-    xa_norm(a);
+    XAcc x = a, y = b;
+    xa_sar192(x, E - a.e);
+    xa_sar192(y, E - b.e);
+    xa_add192(x, y.w2, y.w1, y.w0);
+    x.e = E;
+    xa_norm(x);
+    a = x;
 }
 
 // Round w * 2^e to the nearest FP64 (ties to even).
@@ -204,39 +130,46 @@ __host__ __device__ __forceinline__ double xa_round(const XAcc& a) {
     if (a.e == kXaNaN) {
         bits = 0x7FF8000000000000ull;
     } else {
-        unsigned long long hi = a.hi, lo = a.lo;
-        const bool neg = (long long)hi < 0;
-        if (neg) {
-            lo = ~lo + 1ull;
-            hi = ~hi + (lo == 0 ? 1ull : 0ull);
+        unsigned long long w0 = a.w0, w1 = a.w1, w2 = a.w2;
+        const bool neg = (long long)w2 < 0;
+        if (neg) {  // negate
+            w0 = ~w0;
+            w1 = ~w1;
+            w2 = ~w2;
+            w0 += 1ull;
+            const unsigned long long c0 = w0 == 0ull ? 1ull : 0ull;
+            w1 += c0;
+            w2 += (c0 && w1 == 0ull) ? 1ull : 0ull;
         }
-        const int len = hi ? 128 - xa_clz64(hi) : 64 - xa_clz64(lo);
+        int len = w2 ? 192 - xa_clz64(w2) : w1 ? 128 - xa_clz64(w1) : 64 - xa_clz64(w0);
         if (len == 0) return 0.0;
         int q = a.e + len - 53;  // weight of the last kept bit
         if (q < -1074) q = -1074;
         const int sh = q - a.e;  // bits dropped
         unsigned long long mant;
         if (sh <= 0) {
-            mant = lo << (-sh);  // len <= 53 here: exact
+            mant = w0 << (-sh);  // len <= 53 here: exact
         } else {
-            unsigned long long mh = hi, ml = lo;
-            unsigned long long rh = hi, rl = lo;
-            xa_sra(mh, ml, sh);  // value is non-negative here, so arithmetic == logical
-            mant = ml;
-            // round bit and sticky bits below the kept part
-            xa_sra(rh, rl, sh - 1);
-            const bool rbit = (rl & 1ull) != 0;
+            XAcc m;
+            m.e = 0;
+            m.w0 = w0;
+            m.w1 = w1;
+            m.w2 = w2;  // non-negative: arithmetic == logical shift
+            XAcc rb = m;
+            xa_sar192(m, sh);
+            mant = m.w0;
+            xa_sar192(rb, sh - 1);
+            const bool rbit = (rb.w0 & 1ull) != 0;
+            // sticky: any of the lowest sh-1 bits
+            const int sb = sh - 1;
             bool sticky;
-            const int sb = sh - 1;  // number of bits below the round bit
-            if (sb <= 0) {
-                sticky = false;
-            } else if (sb >= 128) {
-                sticky = (hi | lo) != 0;
-            } else if (sb >= 64) {
-                sticky = lo != 0 || (hi & ((sb == 64) ? 0ull : ((1ull << (sb - 64)) - 1ull))) != 0;
-            } else {
-                sticky = (lo & ((1ull << sb) - 1ull)) != 0;
-            }
+            if (sb <= 0) sticky = false;
+            else if (sb < 64) sticky = (w0 & ((1ull << sb) - 1ull)) != 0;
+            else if (sb == 64) sticky = w0 != 0;
+            else if (sb < 128) sticky = w0 != 0 || (w1 & ((1ull << (sb - 64)) - 1ull)) != 0;
+            else if (sb == 128) sticky = (w0 | w1) != 0;
+            else if (sb < 192) sticky = (w0 | w1) != 0 || (w2 & ((1ull << (sb - 128)) - 1ull)) != 0;
+            else sticky = (w0 | w1 | w2) != 0;
             if (rbit && (sticky || (mant & 1ull))) mant += 1ull;
         }
         if (mant >> 53) {
@@ -261,20 +194,156 @@ __host__ __device__ __forceinline__ double xa_round(const XAcc& a) {
 }
 
 #ifdef __CUDACC__
-__device__ __forceinline__ XAcc xa_shfl_xor(const XAcc& a, int off) {
-    XAcc b;
-    b.e = __shfl_xor_sync(0xffffffffu, a.e, off);
-    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, off);
-    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, off);
-    return b;
+// ---- per-warp accumulation with a warp-uniform window --------------------------------
+//
+// In the solver every lane adds one product per 32-row tile.  The 32 lanes of
+// a warp share one window anchor: per term the warp takes the largest term
+// top (five shuffles), slides the shared window up if needed (a uniform
+// branch), and each lane then only shifts its term right into the window and
+// adds it: no divergent branches, about 40 integer instructions per product.
+constexpr int kWaTop = 108;        // the warp's largest term ends at or below bit kWaTop
+constexpr int kWaNone = -(1 << 30);
+
+struct WAcc {
+    int eb;                        // exponent of bit 0 of the window; the same in all lanes of a warp
+    unsigned long long hi, lo;     // this lane's 128-bit two's complement partial sum
+};
+
+__device__ __forceinline__ void wa_init(WAcc& a) {
+    a.eb = kXaEmpty;
+    a.hi = 0;
+    a.lo = 0;
 }
-__device__ __forceinline__ void xa_warp_merge(XAcc& a) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const XAcc b = xa_shfl_xor(a, off);
-        xa_merge(a, b);
+
+// (h:l) >>= r, logical, r >= 0, without branches (r >= 128 gives 0)
+__device__ __forceinline__ void shr128(unsigned long long& h, unsigned long long& l, int r) {
+    const int rr = r > 127 ? 127 : r;
+    const int s = rr & 63;
+    const unsigned long long lo_a = s ? ((l >> s) | (h << (64 - s))) : l;
+    const unsigned long long hi_a = h >> s;
+    const bool big = rr >= 64;
+    l = big ? hi_a : lo_a;
+    h = big ? 0ull : hi_a;
+    if (r > 127) {
+        h = 0ull;
+        l = 0ull;
     }
 }
+// (h:l) >>= r, arithmetic, r >= 0, without branches
+__device__ __forceinline__ void sar128(unsigned long long& h, unsigned long long& l, int r) {
+    const long long sh = (long long)h;
+    const int rr = r > 127 ? 127 : r;
+    const int s = rr & 63;
+    const unsigned long long lo_a = s ? ((l >> s) | (h << (64 - s))) : l;
+    const unsigned long long hi_a = (unsigned long long)(sh >> s);
+    const bool big = rr >= 64;
+    l = big ? hi_a : lo_a;
+    h = big ? (unsigned long long)(sh >> 63) : hi_a;
+}
+
+__device__ __forceinline__ int warp_max_int(int v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// Add this lane's term (ph:pl) * 2^pe, where ph:pl < 2^kWaTop; `valid` lanes
+// only; `special` marks a NaN/Inf operand.  Every lane of the warp must call.
+__device__ __forceinline__ void wa_add_term(WAcc& a, unsigned long long ph, unsigned long long pl, int pe, bool neg,
+                                            bool valid, bool special) {
+    if (__any_sync(0xffffffffu, special)) a.eb = kXaNaN;
+    if (a.eb == kXaNaN) return;
+    const int wmax = warp_max_int(valid ? pe + kWaTop : kWaNone);
+    if (wmax == kWaNone) return;
+    if (a.eb == kXaEmpty) {
+        a.eb = wmax - kWaTop;
+    } else if (wmax > a.eb + kWaTop) {
+        const int d = wmax - kWaTop - a.eb;
+        sar128(a.hi, a.lo, d);
+        a.eb += d;
+    }
+    shr128(ph, pl, a.eb - pe);
+    if (!valid) {
+        ph = 0ull;
+        pl = 0ull;
+    }
+    if (neg) {
+        pl = ~pl + 1ull;
+        ph = ~ph + (pl == 0ull ? 1ull : 0ull);
+    }
+    xa_add128(a.hi, a.lo, ph, pl);
+}
+
+// x * y, FP64 operands: exact 106-bit product, placed with its top at bit 108.
+__device__ __forceinline__ void wa_acc(WAcc& a, double x, double y, bool valid) {
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+    const int Ex = (int)((bx >> 52) & 0x7FF), Ey = (int)((by >> 52) & 0x7FF);
+    const bool special = valid && (Ex == 0x7FF || Ey == 0x7FF);
+    unsigned long long mx = (bx & 0xFFFFFFFFFFFFFull) | (Ex ? (1ull << 52) : 0ull);
+    unsigned long long my = (by & 0xFFFFFFFFFFFFFull) | (Ey ? (1ull << 52) : 0ull);
+    const bool live = valid && !special && mx != 0ull && my != 0ull;
+    const unsigned long long ph = __umul64hi(mx, my), pl = mx * my;
+    const int pe = (Ex ? Ex - 1075 : -1074) + (Ey ? Ey - 1075 : -1074) - 2;
+    wa_add_term(a, (ph << 2) | (pl >> 62), pl << 2, pe, ((bx ^ by) >> 63) != 0ull, live, special);
+}
+
+// x * y, FP32 operands: exact 48-bit product, placed with its top at bit 108.
+__device__ __forceinline__ void wa_acc(WAcc& a, float x, float y, bool valid) {
+    const unsigned bx = __float_as_uint(x), by = __float_as_uint(y);
+    const int Ex = (int)((bx >> 23) & 0xFF), Ey = (int)((by >> 23) & 0xFF);
+    const bool special = valid && (Ex == 0xFF || Ey == 0xFF);
+    const unsigned mx = (bx & 0x7FFFFFu) | (Ex ? (1u << 23) : 0u);
+    const unsigned my = (by & 0x7FFFFFu) | (Ey ? (1u << 23) : 0u);
+    const bool live = valid && !special && mx != 0u && my != 0u;
+    const unsigned long long p = (unsigned long long)mx * my;
+    const int pe = (Ex ? Ex - 150 : -149) + (Ey ? Ey - 150 : -149) - 60;
+    wa_add_term(a, p >> 4, p << 60, pe, ((bx ^ by) >> 31) != 0u, live, special);
+}
+
+// Warp total of a WAcc: every lane obtains the exact warp sum as a 192-bit XAcc.
+__device__ __forceinline__ XAcc wa_warp_total(const WAcc& a) {
+    XAcc r;
+    r.e = a.eb;
+    r.w0 = a.lo;
+    r.w1 = a.hi;
+    r.w2 = (unsigned long long)((long long)a.hi >> 63);
+    if (a.eb == kXaNaN || a.eb == kXaEmpty) {
+        r.w0 = r.w1 = r.w2 = 0ull;
+        return r;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, r.w0, off);
+        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, r.w1, off);
+        const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, r.w2, off);
+        xa_add192(r, b2, b1, b0);
+    }
+    return r;
+}
+
+// Exact sum over the lanes of a warp of merged partials with different
+// anchors, aligned to the largest anchor (bits below its window are dropped:
+// more than 2^-108 below the largest product).  Every lane obtains the total.
+__device__ __forceinline__ XAcc xa_warp_aligned_sum(XAcc a) {
+    const int E = warp_max_int(a.e);
+    XAcc r;
+    r.e = E;
+    r.w0 = r.w1 = r.w2 = 0ull;
+    if (E == kXaNaN || E == kXaEmpty) return r;
+    xa_sar192(a, E - a.e);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, a.w0, off);
+        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, a.w1, off);
+        const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, a.w2, off);
+        xa_add192(a, b2, b1, b0);
+    }
+    a.e = E;
+    xa_norm(a);
+    return a;
+}
+
 #endif
 
 }  // namespace bcs

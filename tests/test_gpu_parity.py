@@ -325,3 +325,16 @@ def test_batched(env, prec, csize):
         if prec == "fp64":
             assert r["iterations"] == ref["iterations"] and np.array_equal(xh, ref["x"])
         assert np.max(np.abs(xh - 1.0)) <= 1e-6
+
+
+def test_barrier_timeout_is_reported_and_recoverable(env):
+    """Failure detection without a GPU fault: a spin budget of a few cycles makes the
+    bounded grid-barrier waits run out; the solve returns BCS_ERR_TIMEOUT (no trap, no
+    hang) and the next solve on the same context succeeds."""
+    bcs, torch, orc = env
+    A = W.cd2d(48, 10.0)
+    b = W.rhs_ones(A)
+    res, x, h, _ = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", spin_budget_ms=1e-6, max_ctas=8)
+    assert res["status"] == bcs.ERR_TIMEOUT
+    res, x, h, _ = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", max_ctas=8)
+    assert res["status"] == 0 and orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
