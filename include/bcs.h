@@ -167,6 +167,27 @@ int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int ve
  */
 int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result, void* stream);
 
+/*
+ * bcs_dot without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * whose device memory is all owned by another allocator (for example a
+ * framework's caching allocator), or latency-sensitive loops in which a
+ * cudaMalloc/cudaFree (which synchronise the device) would stall.  It computes
+ * the same correctly rounded (x, y) as bcs_dot with the same kernels, but the
+ * per-CTA partial sums go to a fixed 128 KiB array that the library holds on
+ * every GPU that loads it until the process exits (at most 256 CTAs).
+ *   n           number of elements, 0 <= n <= 2^33 (BCS_ERR_ARG beyond that).
+ *   x, y        device vectors, FP64 when vec_f32 == 0, FP32 otherwise.
+ *   result_dev  device double receiving the value; written asynchronously on
+ *               stream (synchronise before reading it).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array, so calls that overlap on the GPU (different streams,
+ * or different host threads on one device) race: serialise them.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ */
+int bcs_dot_noalloc(int64_t n, const void* x, const void* y, int vec_f32, double* result_dev, void* stream);
+
 /* Free a matrix (NULL is ignored).  Waits for the device first. */
 void bcs_matrix_free(bcs_matrix A);
 

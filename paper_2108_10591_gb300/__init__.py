@@ -25,7 +25,7 @@ LAYOUT_CSR, LAYOUT_SELL = 1, 2
 STORE_F64, STORE_F32, STORE_BF16 = 1, 2, 4
 OK, NOT_CONVERGED, ERR_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NONFINITE, ERR_OOM = 0, 1, -1, -2, -3, -4, -5, -6
 
-EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv", "bcs_dot",
+EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv", "bcs_dot", "bcs_dot_noalloc",
             "bcs_matrix_free", "bcs_solver_create", "bcs_solve", "bcs_solve_host", "bcs_get_history",
             "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_status_string"]
 
@@ -63,6 +63,7 @@ def _load():
     L.bcs_matrix_export.argtypes = [P] * 10
     L.bcs_spmv.argtypes = [P, I, I, P, P, I, I, P]
     L.bcs_dot.argtypes = [I64, P, P, I, ctypes.POINTER(D), P]
+    L.bcs_dot_noalloc.argtypes = [I64, P, P, I, P, P]
     L.bcs_matrix_free.argtypes = [P]
     L.bcs_matrix_free.restype = None
     L.bcs_solver_create.argtypes = [P, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
@@ -214,6 +215,15 @@ def dot(x, y, stream=None):
     _check(lib.bcs_dot(x.numel(), _ptr(x), _ptr(y), int(x.dtype == torch.float32), ctypes.byref(out),
                        _stream(stream)), "bcs_dot")
     return out.value
+
+
+def dot_noalloc(x, y, out, stream=None):
+    """bcs_dot_noalloc: (x, y) of two torch CUDA tensors into the one-element float64 CUDA
+    tensor `out`, asynchronously, with no device allocation."""
+    import torch
+    _check(lib.bcs_dot_noalloc(x.numel(), _ptr(x), _ptr(y), int(x.dtype == torch.float32), _ptr(out),
+                               _stream(stream)), "bcs_dot_noalloc")
+    return out
 
 
 class Solver:

@@ -113,11 +113,12 @@ __device__ __forceinline__ void prefetch_partials(const unsigned long long* base
 }
 
 // Sum every CTA's record exactly (all CTAs obtain the same values) and round
-// each slot once: out[k] = correctly rounded slot k.
+// each slot once: out[k] = correctly rounded slot k, for the first NS slots.
+template <int NS = 10>
 __device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage& st, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 1
-    for (int k = 0; k < 10; ++k) {
+    for (int k = 0; k < NS; ++k) {
         XAcc a;
         xa_init(a);
         for (int c = threadIdx.x; c < nblk; c += kBlock) {
@@ -129,7 +130,7 @@ __device__ __forceinline__ void reduce_partials(const unsigned long long* base, 
     __syncthreads();
     if (warp == 0) {
 #pragma unroll 1
-        for (int k = 0; k < 10; ++k) {
+        for (int k = 0; k < NS; ++k) {
             XAcc t;
             if (lane < kWarps) t = st.w[k][lane]; else xa_init(t);
             t = xa_warp_aligned_sum(t);
