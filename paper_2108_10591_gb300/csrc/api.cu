@@ -176,7 +176,9 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
         if (rc) return;
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) rc = BCS_ERR_OOM;
     };
-    alloc(&s->vecmem, (size_t)NVEC * nn * s->vbytes);
+    // vectors padded to whole 32-row tiles: the staging copies move full tiles
+    const int64_t npad = ((n + 31) / 32) * 32 > 0 ? ((n + 31) / 32) * 32 : 32;
+    alloc(&s->vecmem, (size_t)NVEC * npad * s->vbytes);
     if (s->layout == LAY_SELL) {
         alloc((void**)&s->x64w, sizeof(double) * nn);
         alloc((void**)&s->b64w, sizeof(double) * nn);
@@ -232,8 +234,8 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
     P->val = inner_values(A, s->layout, s->valtype);
     P->b = b;
     P->x = x;
-    const size_t nn = (size_t)std::max<int64_t>(A->n, 1);
-    for (int v = 0; v < NVEC; ++v) P->vec[v] = (char*)s->vecmem + (size_t)v * nn * s->vbytes;
+    const size_t npad = (size_t)std::max<int64_t>(((A->n + 31) / 32) * 32, 32);
+    for (int v = 0; v < NVEC; ++v) P->vec[v] = (char*)s->vecmem + (size_t)v * npad * s->vbytes;
     P->partials = s->partials;
     P->bar = s->bar;
     P->err = (int*)(s->bar + 4);
@@ -391,10 +393,11 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
     std::vector<double> hout((size_t)nsys * NOUT);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms = 0.f;
+    int herr = 0;
     auto ck = [&](cudaError_t e) { if (e != cudaSuccess && !rc) rc = BCS_ERR_CUDA; };
     ck(cudaMalloc(&dsys, sizeof(KParams) * nsys));
     ck(cudaMalloc(&dorder, sizeof(int) * nsys));
-    ck(cudaMalloc(&dctl, sizeof(int) * (1 + nclusters)));
+    ck(cudaMalloc(&dctl, sizeof(int) * (2 + nclusters)));  // counter, slots[nclusters], error word
     if (!rc && cudaMalloc(&ws, B.ws_group_bytes * nclusters) != cudaSuccess) rc = BCS_ERR_OOM;
     ck(cudaMalloc(&parts, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters));
     ck(cudaMalloc(&outs, sizeof(double) * NOUT * nsys));
@@ -425,10 +428,11 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
             P.x64 = x[k];
             P.b64 = b[k];
             P.out = outs + (size_t)k * NOUT;
+            P.err = dctl + 1 + nclusters;
         }
         ck(cudaMemcpyAsync(dsys, hp.data(), sizeof(KParams) * nsys, cudaMemcpyHostToDevice, st));
         ck(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-        ck(cudaMemsetAsync(dctl, 0, sizeof(int) * (1 + nclusters), st));
+        ck(cudaMemsetAsync(dctl, 0, sizeof(int) * (2 + nclusters), st));
         ck(cudaMemsetAsync(outs, 0, sizeof(double) * NOUT * nsys, st));
         ck(cudaMemsetAsync(parts, 0, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters, st));
         ck(cudaEventCreate(&e0));
@@ -445,10 +449,11 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
         if (dispatch_b(&B, vt_f32, valtype, tpr, nclusters, st, nullptr) != 0) rc = BCS_ERR_CUDA;
         cudaEventRecord(e1, st);
         ck(cudaMemcpyAsync(hout.data(), outs, sizeof(double) * NOUT * nsys, cudaMemcpyDeviceToHost, st));
+        ck(cudaMemcpyAsync(&herr, dctl + 1 + nclusters, sizeof(int), cudaMemcpyDeviceToHost, st));
         ck(cudaStreamSynchronize(st));
         cudaEventElapsedTime(&ms, e0, e1);
     }
-    int worst = BCS_OK;
+    int worst = herr ? herr : BCS_OK;
     if (!rc) {
         for (int k = 0; k < nsys; ++k) {
             const double* ob = hout.data() + (size_t)k * NOUT;

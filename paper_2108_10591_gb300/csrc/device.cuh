@@ -111,6 +111,98 @@ template <> struct VecOf<double> { typedef double type; };
 __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 
+// ---- TMA bulk copies into shared memory with mbarrier completion ----------------------
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// arrive (count 1) and announce `bytes` of transactions for the current phase
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// bulk copy global -> this CTA's shared memory, completing on bar (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// order this thread's earlier generic-proxy accesses before later async-proxy (TMA) accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// bounded wait for the completion of phase `parity` of bar; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long budget) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
+// Per-warp double-buffered staging of the 32-row chunks of up to kMaxStage
+// vectors.  Lane 0 issues one bulk copy per vector into a stage and arms the
+// stage's mbarrier with the byte count; lanes wait on the barrier (bounded)
+// and read their row from shared memory.  Vectors must be padded to whole
+// 32-row tiles (the solver's arena is).
+constexpr int kMaxStage = 12;
+
+template <class VT>
+struct WarpStager {
+    VT* buf;                   // [2][kMaxStage][32] in shared memory
+    unsigned long long* bar;   // [2] mbarriers
+    unsigned parity;           // bit s: parity of stage s's next completion
+    unsigned pending;          // bit s: a copy into stage s has not been seen complete
+    bool dead;                 // a wait timed out (warp-uniform): issue and wait no more
+
+    template <int K>
+    __device__ __forceinline__ void issue(const VT* const (&v)[K], int64_t tile, int stage) {
+        if (dead) return;
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long* b = bar + stage;
+            mbar_arrive_tx(b, (unsigned)(K * 32 * sizeof(VT)));
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                bulk_g2s(buf + (stage * kMaxStage + k) * 32, v[k] + tile * 32, 32 * sizeof(VT), b);
+        }
+        pending |= 1u << stage;
+    }
+    // wait for `stage`; returns the stage's shared-memory rows (element [k*32 + lane])
+    __device__ __forceinline__ const VT* wait(int stage, long long budget, int* err) {
+        if (!dead) {
+            const bool ok = mbar_wait(bar + stage, (parity >> stage) & 1u, budget);
+            if (__any_sync(kFull, !ok)) {
+                dead = true;
+                if ((threadIdx.x & 31) == 0 && err) atomicCAS(err, 0, (int)BCS_ERR_TIMEOUT);
+            } else {
+                pending &= ~(1u << stage);
+            }
+        }
+        parity ^= 1u << stage;
+        return buf + stage * kMaxStage * 32;
+    }
+    // consume every stage that was issued but not waited for (a phase that was
+    // abandoned after its prologue), keeping the parities in step
+    __device__ __forceinline__ void settle(long long budget, int* err) {
+#pragma unroll
+        for (int st = 0; st < 2; ++st)
+            if ((pending >> st) & 1u) wait(st, budget, err);
+    }
+    // before leaving the kernel: wait (bounded) for copies still in flight
+    __device__ __forceinline__ void drain(long long budget) {
+#pragma unroll
+        for (int st = 0; st < 2; ++st)
+            if ((pending >> st) & 1u) mbar_wait(bar + st, (parity >> st) & 1u, budget);
+        pending = 0u;
+    }
+};
+
 // ---- SpMV on a tile of 32 consecutive rows (lane k -> row row0+k) -----------------
 
 // CSR with T lanes per row.  T == 1: each lane sums its row sequentially in

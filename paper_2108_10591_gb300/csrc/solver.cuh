@@ -208,6 +208,39 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     auto rbase = [&](int buf) -> unsigned long long* { return precs + (size_t)buf * nblk * NSLOT * kRec; };
     auto myrec = [&](int buf) -> unsigned long long* { return rbase(buf) + (size_t)rank * NSLOT * kRec; };
 
+    // Per-warp TMA staging of the row-local vector chunks of the warp's next tiles
+    // (double-buffered in dynamic shared memory; see WarpStager).
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    WarpStager<VT> stg;
+    stg.buf = (VT*)(s_dyn + (size_t)warp * 2 * kMaxStage * 32 * sizeof(VT));
+    stg.bar = (unsigned long long*)(s_dyn + (size_t)kWarps * 2 * kMaxStage * 32 * sizeof(VT)) + 2 * warp;
+    stg.parity = 0u;
+    stg.pending = 0u;
+    stg.dead = false;
+    if (lane == 0) {
+        mbar_init(stg.bar, 1);
+        mbar_init(stg.bar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // bounded wait for in-flight staging copies on an error exit (about 0.5 s)
+    constexpr long long kDrainBudget = 1000000000ll;
+    // issue the warp's first two tiles of a phase (after the grid barrier that
+    // made the previous phase's writes visible)
+    auto stage_pro = [&](const auto& v) {
+        if (lane == 0) fence_proxy_async();
+        if (gwarp < ntiles) stg.issue(v, gwarp, 0);
+        if (gwarp + nwarps < ntiles) stg.issue(v, gwarp + nwarps, 1);
+    };
+    // after a tile's rows were read: refill its stage with the tile two ahead
+    auto stage_next = [&](const auto& v, int64_t tile, int64_t kt) {
+        __syncwarp();
+        if (tile + 2 * nwarps < ntiles) {
+            if (lane == 0) fence_proxy_async();
+            stg.issue(v, tile + 2 * nwarps, (int)(kt & 1));
+        }
+    };
+
     // ---- SELL: the solve runs in the permuted row order ----
     if (P.perm != nullptr) {
         for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -218,7 +251,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 P.b64w[row] = P.b[src];
             }
         }
-        if (!grp.sync(&s_flag)) return;
+        if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
     }
 
     int status = BCS_NOT_CONVERGED, inner_status = BCS_OK;
@@ -260,7 +293,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             xv[SR] = xv[SF];
             flush_partials<(1u << ST) | (1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(
                 xv, s_x, myrec(0));
-            if (!grp.sync(&s_flag)) return;
+            if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
             prefetch_partials(rbase(0), nblk);
             reduce_partials(rbase(0), nblk, s_x, s_sum);
             const double rt2 = s_sum[ST];
@@ -304,7 +337,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_acc(xv[SG], qa_SG, qb_SG, row < n);
             }
             flush_partials<(1u << SA) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(0));
-            if (!grp.sync(&s_flag)) return;
+            if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
         }
 
         // ---------------- iterations ----------------------------------------------------------
@@ -317,8 +350,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             if (kind == BCS_SSBICGSAFE2) {
                 // phase A: s_i = A r_i and the products involving s_i
                 wa_init10(xv);
-                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const VT* const vPA[] = {Y, R, RS};
+                stage_pro(vPA);
+                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
                     const VT sv = spmv(R, tile);
+                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
@@ -326,7 +362,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
                         sCur[row] = sv;
-                        const VT yv = Y[row], rv = R[row], rsv = RS[row];
+                        const VT yv = sm[lane], rv = sm[32 + lane], rsv = sm[64 + lane];
                         qa_SA = sv;
                         qb_SA = sv;
                         qa_SC = sv;
@@ -340,15 +376,20 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                    stage_next(vPA, tile, kt);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(cur));
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 prefetch_partials(rbase(cur), nblk);
             } else {
                 // phase A: the partials of iteration i travel to L1 while A s_i of the
                 // first tile is computed (the overlap of the reduction with MV, Section 3)
                 prefetch_partials(rbase(cur), nblk);
-                if (!rr_step && gwarp < ntiles) as_first = spmv(sCur, gwarp);
+                if (!rr_step) {
+                    const VT* const vA0[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
+                    stage_pro(vA0);
+                    if (gwarp < ntiles) as_first = spmv(sCur, gwarp);
+                }
             }
             reduce_partials(rbase(cur), nblk, s_x, s_sum);
 
@@ -411,27 +452,39 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 alpha_p = alpha; zeta_p = zeta; f_p = f;
             }
             __syncthreads();
-            if (s_ctl[0]) { inner_status = s_ctl[1]; break; }
+            if (s_ctl[0]) {
+                // the run stops here: the staged first tiles of this phase A are not used
+                stg.settle(P.spin_budget, P.err);
+                inner_status = s_ctl[1];
+                break;
+            }
             const VT al = (VT)s_sc[0], be = (VT)s_sc[1], ze = (VT)s_sc[2], et = (VT)s_sc[3];
 
             if (kind == BCS_SSBICGSAFE2) {
                 // phase B: p_i, o_i, u_i
-                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const VT* const vPB[] = {R, sCur, Tv, Y, Pv, U};
+                stage_pro(vPB);
+                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
+                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     if (row < n) {
-                        const VT r = R[row], s = sCur[row], t = Tv[row], y = Y[row];
-                        VT p = Pv[row], u = U[row];
+                        const VT r = sm[lane], s = sm[32 + lane], t = sm[64 + lane], y = sm[96 + lane];
+                        VT p = sm[128 + lane], u = sm[160 + lane];
                         p = vfma(be, p - u, r);
                         const VT o = vfma(be, t, s);
                         u = vfma(ze, o, et * vfma(be, u, y));
                         Pv[row] = p; O[row] = o; U[row] = u;
                     }
+                    stage_next(vPB, tile, kt);
                 }
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
                 wa_init10(xv);
-                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const VT* const vPC[] = {O, R, U, sCur, Y, Pv, RS, Z};
+                stage_pro(vPC);
+                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
                     const VT w = spmv(U, tile);
+                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
@@ -439,8 +492,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     VT qa_SH = VT(0), qb_SH = VT(0);
                     VT qa_SR = VT(0), qb_SR = VT(0);
                     if (row < n) {
-                        const VT o = O[row], r = R[row], u = U[row], s = sCur[row], y = Y[row], p = Pv[row], rs = RS[row];
-                        VT z = Z[row], x = X[row];
+                        const VT o = sm[lane], r = sm[32 + lane], u = sm[64 + lane], s = sm[96 + lane];
+                        const VT y = sm[128 + lane], p = sm[160 + lane], rs = sm[192 + lane];
+                        VT z = sm[224 + lane], x = X[row];
                         const VT t = o - w;
                         z = vfma(-al, u, vfma(ze, r, et * z));
                         const VT yn = vfma(-al, w, vfma(ze, s, et * y));
@@ -463,14 +517,17 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    stage_next(vPC, tile, kt);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
             } else if (!rr_step) {
                 // phase A (continued): fused recurrences of Alg. 4
                 wa_init10(xv);
-                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const VT* const vA[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
+                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
                     const VT As = (tile == gwarp) ? as_first : spmv(sCur, tile);
+                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
@@ -478,9 +535,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     VT qa_SH = VT(0), qb_SH = VT(0);
                     VT qa_SR = VT(0), qb_SR = VT(0);
                     if (row < n) {
-                        const VT r = R[row], s = sCur[row], rs = RS[row];
-                        VT p = Pv[row], u = U[row], t = Tv[row], l = L[row], y = Y[row], g = G[row];
-                        VT w = W[row], z = Z[row], x = X[row];
+                        const VT r = sm[lane], s = sm[32 + lane], rs = sm[64 + lane];
+                        VT p = sm[96 + lane], u = sm[128 + lane], t = sm[160 + lane], l = sm[192 + lane];
+                        VT y = sm[224 + lane], g = sm[256 + lane], w = sm[288 + lane], z = sm[320 + lane];
+                        VT x = X[row];
                         p = vfma(be, p - u, r);
                         const VT o = vfma(be, t, s);
                         u = vfma(ze, o, et * vfma(be, u, y));
@@ -511,25 +569,29 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    stage_next(vA, tile, kt);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
                 wa_init10(xv);
-                for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const VT* const vC[] = {L, G, sNxt, Y, R, RS};
+                stage_pro(vC);
+                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
                     const VT Aw = spmv(W, tile);
+                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
                     VT qa_SD = VT(0), qb_SD = VT(0);
                     VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
-                        const VT q = L[row], gp = G[row], sa = sNxt[row];
+                        const VT q = sm[lane], gp = sm[32 + lane], sa = sm[64 + lane];
                         const VT l = q - Aw;
                         const VT g = vfma(-al, Aw, gp);
                         const VT s = sa - g;
                         L[row] = l; G[row] = g; sNxt[row] = s;
-                        const VT y = Y[row], r = R[row], rs = RS[row];
+                        const VT y = sm[96 + lane], r = sm[128 + lane], rs = sm[160 + lane];
                         qa_SA = s;
                         qb_SA = s;
                         qa_SC = s;
@@ -543,9 +605,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                    stage_next(vC, tile, kt);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
             } else {
                 // residual replacement iteration (Alg. 5)
@@ -560,7 +623,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         Pv[row] = p; O[row] = o; U[row] = u;
                     }
                 }
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // w_i = A u_i (q_i = A o_i is not used after a replacement); t, z, y_{i+1}, x_{i+1}
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT w = spmv(U, tile);
@@ -575,7 +638,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         W[row] = w; Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x;
                     }
                 }
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // r_{i+1} = b - A x_{i+1}; l_i = A t_i; g_{i+1} = A y_{i+1}
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -610,7 +673,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // s_{i+1} = A r_{i+1}
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -638,7 +701,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) return;
+                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 ++rr_steps;
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
             }
@@ -651,7 +714,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 if (row < n) P.x64[row] += (double)X[row];
             }
         }
-        if (!grp.sync(&s_flag)) return;
+        if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
     }
 
     if (rank == 0 && threadIdx.x == 0) {
@@ -679,11 +742,21 @@ __global__ void __launch_bounds__(kBlock, 3) solve_kernel(const __grid_constant_
     solve_body<VT, MT, LAYOUT, T>(P, grp);
 }
 
+// dynamic shared memory of the solver kernels: the per-warp staging buffers and their mbarriers
+template <class VT>
+constexpr size_t stage_smem_bytes() {
+    return (size_t)kWarps * 2 * kMaxStage * 32 * sizeof(VT) + (size_t)kWarps * 2 * sizeof(unsigned long long);
+}
+
 template <class VT, class MT, int LAYOUT, int T>
 int launch_one(const KParams& P, int grid, cudaStream_t st) {
     void* args[] = {(void*)&P};
+    const size_t smem = stage_smem_bytes<VT>();
+    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T>, dim3(grid), dim3(kBlock),
-                                            args, 0, st);
+                                            args, smem, st);
 }
 
 template <class VT, class MT, int LAYOUT, int T>
@@ -691,8 +764,12 @@ int max_grid_one(int* grid) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = stage_smem_bytes<VT>();
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T>, kBlock, 0);
+        e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T>, kBlock, smem);
     *grid = sms * per;
     return (int)e;
 }
@@ -786,13 +863,15 @@ int dispatch_batched(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = stage_smem_bytes<VT>();
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void (*fn)(BatchArgs) = (tpr == 1) ? batched_kernel<VT, MT, 1> : batched_kernel<VT, MT, 8>;
-    cudaError_t e = cudaSuccess;
-    if (B->csize > 8) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)stage_smem_bytes<VT>());
+    if (e == cudaSuccess && B->csize > 8)
+        e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
     if (max_clusters) {
         int dev = 0, sms = 0;
