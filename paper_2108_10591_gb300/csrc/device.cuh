@@ -147,63 +147,58 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // Per-warp double-buffered staging of the 32-row chunks of up to kMaxStage
-// vectors.  Lane 0 issues one bulk copy per vector into a stage and arms the
-// stage's mbarrier with the byte count; lanes wait on the barrier (bounded)
-// and read their row from shared memory.  Vectors must be padded to whole
-// 32-row tiles (the solver's arena is).
+// vectors.  Every lane copies its own row of each vector with cp.async
+// (global -> shared without going through registers, coalesced across the
+// warp like a load) and commits one group per stage; a lane waits only for
+// its own copies (cp.async.wait_group) and reads back only its own row, so no
+// cross-lane synchronisation and no spin is involved.  The source vectors
+// must be padded to whole 32-row tiles (the solver's arena is).
 constexpr int kMaxStage = 12;
+
+template <class VT>
+__device__ __forceinline__ void cp_async_elem(VT* dst, const VT* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(sizeof(VT))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <class VT>
 struct WarpStager {
     VT* buf;                   // [2][kMaxStage][32] in shared memory
-    unsigned long long* bar;   // [2] mbarriers
-    unsigned parity;           // bit s: parity of stage s's next completion
-    unsigned pending;          // bit s: a copy into stage s has not been seen complete
-    bool dead;                 // a wait timed out (warp-uniform): issue and wait no more
+    unsigned long long* bar;   // unused (kept for the layout)
+    unsigned parity;           // unused
+    unsigned pending;          // bit s: stage s has a committed group not yet waited for
+    bool dead;                 // unused
 
     template <int K>
     __device__ __forceinline__ void issue(const VT* const (&v)[K], int64_t tile, int stage) {
-        if (dead) return;
-        if ((threadIdx.x & 31) == 0) {
-            unsigned long long* b = bar + stage;
-            mbar_arrive_tx(b, (unsigned)(K * 32 * sizeof(VT)));
+        const int lane = threadIdx.x & 31;
 #pragma unroll
-            for (int k = 0; k < K; ++k)
-                bulk_g2s(buf + (stage * kMaxStage + k) * 32, v[k] + tile * 32, 32 * sizeof(VT), b);
-        }
+        for (int k = 0; k < K; ++k) cp_async_elem(buf + (stage * kMaxStage + k) * 32 + lane, v[k] + tile * 32 + lane);
+        cp_async_commit();
         pending |= 1u << stage;
     }
-    // wait for `stage`; returns the stage's shared-memory rows (element [k*32 + lane])
-    __device__ __forceinline__ const VT* wait(int stage, long long budget, int* err) {
-        if (!dead) {
-            const bool ok = mbar_wait(bar + stage, (parity >> stage) & 1u, budget);
-            if (__any_sync(kFull, !ok)) {
-                dead = true;
-                if ((threadIdx.x & 31) == 0 && err) atomicCAS(err, 0, (int)BCS_ERR_TIMEOUT);
-            } else {
-                pending &= ~(1u << stage);
-            }
-        }
-        parity ^= 1u << stage;
+    // wait for `stage` (the older of the two in flight when `other` is pending)
+    __device__ __forceinline__ const VT* wait(int stage, long long, int*) {
+        if ((pending >> (stage ^ 1)) & 1u) cp_async_wait<1>(); else cp_async_wait<0>();
+        pending &= ~(1u << stage);
         return buf + stage * kMaxStage * 32;
     }
-    // consume every stage that was issued but not waited for (a phase that was
-    // abandoned after its prologue), keeping the parities in step
-    __device__ __forceinline__ void settle(long long budget, int* err) {
-#pragma unroll
-        for (int st = 0; st < 2; ++st)
-            if ((pending >> st) & 1u) wait(st, budget, err);
+    __device__ __forceinline__ void settle(long long, int*) {
+        cp_async_wait<0>();
+        pending = 0u;
     }
-    // before leaving the kernel: wait (bounded) for copies still in flight
-    __device__ __forceinline__ void drain(long long budget) {
-#pragma unroll
-        for (int st = 0; st < 2; ++st)
-            if ((pending >> st) & 1u) mbar_wait(bar + st, (parity >> st) & 1u, budget);
+    __device__ __forceinline__ void drain(long long) {
+        cp_async_wait<0>();
         pending = 0u;
     }
 };
 
 // ---- SpMV on a tile of 32 consecutive rows (lane k -> row row0+k) -----------------
+
+constexpr int kSpmvBatch = 8;  // entries per lane whose loads are in flight together
 
 // CSR with T lanes per row.  T == 1: each lane sums its row sequentially in
 // storage order with fma (the same order as a plain CSR loop).  T > 1: the
@@ -222,9 +217,25 @@ __device__ __forceinline__ VT csr_tile(const int32_t* __restrict__ rowptr, const
         rp1 = __ldg(rowptr + row + 1);
     }
     if constexpr (T == 1) {
+        // Batches of kSpmvBatch entries: all column and value loads of the batch are
+        // issued, then all gathers, then the fmas in storage order -- two memory
+        // rounds per batch instead of two per entry, same rounding as a plain loop.
         VT acc = VT(0);
-#pragma unroll 4
-        for (int k = rp0; k < rp1; ++k) acc = vfma((VT)ldv(val + k), x[__ldg(col + k)], acc);
+        for (int k0 = rp0; k0 < rp1; k0 += kSpmvBatch) {
+            int c[kSpmvBatch];
+            VT v[kSpmvBatch], xv[kSpmvBatch];
+#pragma unroll
+            for (int j = 0; j < kSpmvBatch; ++j) {
+                const bool in = k0 + j < rp1;
+                c[j] = in ? __ldg(col + k0 + j) : 0;
+                v[j] = in ? (VT)ldv(val + k0 + j) : VT(0);
+            }
+#pragma unroll
+            for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + j < rp1) ? x[c[j]] : VT(0);
+#pragma unroll
+            for (int j = 0; j < kSpmvBatch; ++j)
+                if (k0 + j < rp1) acc = vfma(v[j], xv[j], acc);
+        }
         return acc;
     } else {
         constexpr int G = 32 / T;
@@ -258,8 +269,21 @@ __device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, c
     const int lane = threadIdx.x & 31;
     const int64_t b = __ldg(slice_ptr + slice), e = __ldg(slice_ptr + slice + 1);
     VT acc = VT(0);
-#pragma unroll 4
-    for (int64_t k = b + lane; k < e; k += 32) acc = vfma((VT)ldv(sval + k), x[__ldg(scol + k)], acc);
+    for (int64_t k0 = b + lane; k0 < e; k0 += 32 * kSpmvBatch) {  // batched as in csr_tile
+        int c[kSpmvBatch];
+        VT v[kSpmvBatch], xv[kSpmvBatch];
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j) {
+            const bool in = k0 + 32 * j < e;
+            c[j] = in ? __ldg(scol + k0 + 32 * j) : 0;
+            v[j] = in ? (VT)ldv(sval + k0 + 32 * j) : VT(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + 32 * j < e) ? x[c[j]] : VT(0);
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j)
+            if (k0 + 32 * j < e) acc = vfma(v[j], xv[j], acc);
+    }
     return acc;
 }
 

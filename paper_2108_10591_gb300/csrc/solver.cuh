@@ -49,7 +49,8 @@ struct XStage {
     XAcc w[10][kWarps];
 };
 
-__device__ __forceinline__ void wa_init10(WAcc (&a)[10]) {
+template <class ACC>
+__device__ __forceinline__ void wa_init10(ACC (&a)[10]) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) wa_init(a[k]);
 }
@@ -71,8 +72,8 @@ __device__ __forceinline__ XAcc load_rec(const unsigned long long* r) {
 
 // Sum the CTA's warp accumulators of the slots in MASK exactly and store them
 // as the CTA's record; slots in ZMASK are recorded as empty (zero).
-template <unsigned MASK, unsigned ZMASK = 0u>
-__device__ __forceinline__ void flush_partials(WAcc (&a)[10], XStage& st, unsigned long long* rec) {
+template <unsigned MASK, unsigned ZMASK = 0u, class ACC>
+__device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage& st, unsigned long long* rec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
@@ -208,8 +209,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     auto rbase = [&](int buf) -> unsigned long long* { return precs + (size_t)buf * nblk * NSLOT * kRec; };
     auto myrec = [&](int buf) -> unsigned long long* { return rbase(buf) + (size_t)rank * NSLOT * kRec; };
 
-    // Per-warp TMA staging of the row-local vector chunks of the warp's next tiles
-    // (double-buffered in dynamic shared memory; see WarpStager).
+    // Per-warp asynchronous staging of the row-local vector chunks of the warp's
+    // next tiles (double-buffered in dynamic shared memory; see WarpStager).
     extern __shared__ __align__(128) unsigned char s_dyn[];
     WarpStager<VT> stg;
     stg.buf = (VT*)(s_dyn + (size_t)warp * 2 * kMaxStage * 32 * sizeof(VT));
@@ -217,28 +218,18 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     stg.parity = 0u;
     stg.pending = 0u;
     stg.dead = false;
-    if (lane == 0) {
-        mbar_init(stg.bar, 1);
-        mbar_init(stg.bar + 1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
+
     // bounded wait for in-flight staging copies on an error exit (about 0.5 s)
     constexpr long long kDrainBudget = 1000000000ll;
     // issue the warp's first two tiles of a phase (after the grid barrier that
     // made the previous phase's writes visible)
     auto stage_pro = [&](const auto& v) {
-        if (lane == 0) fence_proxy_async();
         if (gwarp < ntiles) stg.issue(v, gwarp, 0);
         if (gwarp + nwarps < ntiles) stg.issue(v, gwarp + nwarps, 1);
     };
     // after a tile's rows were read: refill its stage with the tile two ahead
     auto stage_next = [&](const auto& v, int64_t tile, int64_t kt) {
-        __syncwarp();
-        if (tile + 2 * nwarps < ntiles) {
-            if (lane == 0) fence_proxy_async();
-            stg.issue(v, tile + 2 * nwarps, (int)(kt & 1));
-        }
+        if (tile + 2 * nwarps < ntiles) stg.issue(v, tile + 2 * nwarps, (int)(kt & 1));
     };
 
     // ---- SELL: the solve runs in the permuted row order ----
@@ -264,8 +255,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     for (;;) {
         // ---------------- true residual r = b - A x (FP64) and (re)initialisation ----------
         {
-            WAcc xv[10];
+            typename DotAccOf<VT>::type xv[10];
             wa_init10(xv);
+            WAcc xt[10];  // the FP64 true-residual norm is always accumulated exactly
+            wa_init10(xt);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const double ax = spmv64(P.x64, tile);
                 const int64_t row = tile * 32 + lane;
@@ -287,12 +280,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     qa_SF = rv;
                     qb_SF = rv;
                 }
-                wa_acc(xv[ST], qa_ST, qb_ST, row < n);
+                wa_acc(xt[ST], qa_ST, qb_ST, row < n);
                 wa_acc(xv[SF], qa_SF, qb_SF, row < n);
             }
             xv[SR] = xv[SF];
-            flush_partials<(1u << ST) | (1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(
-                xv, s_x, myrec(0));
+            flush_partials<(1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(xv, s_x,
+                                                                                                    myrec(0));
+            flush_partials<(1u << ST)>(xt, s_x, myrec(0));
             if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
             prefetch_partials(rbase(0), nblk);
             reduce_partials(rbase(0), nblk, s_x, s_sum);
@@ -314,7 +308,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 
         // ---------------- pipelined set-up: s_0 = A r_0 and the i = 0 products --------------
         if (kind != BCS_SSBICGSAFE2) {
-            WAcc xv[10];
+            typename DotAccOf<VT>::type xv[10];
             wa_init10(xv);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const VT sv = spmv(R, tile);
@@ -345,7 +339,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         for (;; ++i) {
             const int cur = i & 1, nxt = cur ^ 1;
             const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
-            WAcc xv[10];
+            typename DotAccOf<VT>::type xv[10];
             VT as_first = VT(0);
             if (kind == BCS_SSBICGSAFE2) {
                 // phase A: s_i = A r_i and the products involving s_i

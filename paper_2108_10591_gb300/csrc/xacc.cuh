@@ -344,6 +344,60 @@ __device__ __forceinline__ XAcc xa_warp_aligned_sum(XAcc a) {
     return a;
 }
 
+
+// ---- FP64 per-lane accumulation (refinement modes: FP32 vectors) --------------------
+// The inner products of the FP32 inner solves accumulate in FP64: each lane
+// adds the exact product of its two FP32 operands (exact in FP64) with one
+// FP64 fma; the lane sums are then merged exactly like the integer partials.
+struct DAcc {
+    double s;
+};
+__device__ __forceinline__ void wa_init(DAcc& a) { a.s = 0.0; }
+
+// FP32 -> FP64 widening with integer operations for normal numbers and zero
+// (keeping the FP64 pipe for the fma); other values use the conversion unit.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) return (double)f;  // zero, subnormal, inf, nan
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ void wa_acc(DAcc& a, float x, float y, bool valid) {
+    if (valid) a.s = fma(widen(x), widen(y), a.s);
+}
+
+// exact 192-bit representation of a double
+__device__ __forceinline__ XAcc xa_from_double(double d) {
+    XAcc r;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int E = (int)((b >> 52) & 0x7FF);
+    r.w2 = r.w1 = r.w0 = 0ull;
+    if (E == 0x7FF) {
+        r.e = kXaNaN;
+        return r;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+    if (m == 0ull) {
+        r.e = kXaEmpty;
+        return r;
+    }
+    r.e = E ? E - 1075 : -1074;
+    r.w0 = m;
+    if (b >> 63) {  // negate
+        r.w0 = ~r.w0 + 1ull;
+        r.w1 = ~0ull;
+        r.w2 = ~0ull;
+    }
+    return r;
+}
+__device__ __forceinline__ XAcc wa_warp_total(const DAcc& a) { return xa_warp_aligned_sum(xa_from_double(a.s)); }
+
+// per-lane accumulator type of a solve: exact integer windows for FP64
+// vectors, FP64 sums for FP32 vectors
+template <class VT> struct DotAccOf { typedef WAcc type; };
+template <> struct DotAccOf<float> { typedef DAcc type; };
 #endif
 
 }  // namespace bcs
