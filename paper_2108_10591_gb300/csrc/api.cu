@@ -164,10 +164,10 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     int grid = maxg;
     if (o.ctas_per_sm > 0) grid = std::min(grid, o.ctas_per_sm * sms);
     if (o.max_ctas > 0) grid = std::min(grid, o.max_ctas);
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (ntiles + kWarps - 1) / kWarps));
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (ntiles + kSolveWarps - 1) / kSolveWarps));
     // each lane's exact inner-product partial holds one product per tile: keep
     // the tiles per warp below 2^16 so that it cannot overflow its 128 bits
-    if ((ntiles + (int64_t)grid * kWarps - 1) / ((int64_t)grid * kWarps) >= (1 << 16)) {
+    if ((ntiles + (int64_t)grid * kSolveWarps - 1) / ((int64_t)grid * kSolveWarps) >= (1 << 16)) {
         delete s;
         return BCS_ERR_ARG;
     }

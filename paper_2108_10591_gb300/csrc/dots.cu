@@ -13,7 +13,7 @@ namespace {
 
 template <class VT>
 __global__ void __launch_bounds__(kBlock) k_dot_partial(int64_t n, const VT* x, const VT* y, unsigned long long* recs) {
-    __shared__ XStage s_x;
+    __shared__ XStage<kWarps> s_x;
     WAcc a[10];
     wa_init10(a);
     const int lane = threadIdx.x & 31;
@@ -26,9 +26,9 @@ __global__ void __launch_bounds__(kBlock) k_dot_partial(int64_t n, const VT* x, 
 }
 
 __global__ void __launch_bounds__(kBlock) k_dot_final(const unsigned long long* recs, int nblk, double* out) {
-    __shared__ XStage s_x;
+    __shared__ XStage<kWarps> s_x;
     __shared__ double s_out[10];
-    reduce_partials(recs, nblk, s_x, s_out);
+    reduce_partials<1>(recs, nblk, s_x, s_out);
     if (threadIdx.x == 0) *out = s_out[0];
 }
 
@@ -82,7 +82,7 @@ unsigned long long* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
 __global__ void __launch_bounds__(kBlock) k_dot_final1(const unsigned long long* recs, int nblk, double* out) {
-    __shared__ XStage s_x;
+    __shared__ XStage<kWarps> s_x;
     __shared__ double s_out[10];
     reduce_partials<1>(recs, nblk, s_x, s_out);
     if (threadIdx.x == 0) *out = s_out[0];

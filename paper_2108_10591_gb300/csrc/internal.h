@@ -21,8 +21,12 @@ enum Out { O_STATUS = 0, O_ITERS, O_OUTER, O_RR, O_FALLBACK, O_RECREL, O_TRUEREL
 enum Layout { LAY_CSR = 0, LAY_SELL = 1 };
 enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
 
-constexpr int kBlock = 256;            // threads per CTA of the solver kernels
+constexpr int kBlock = 256;            // threads per CTA of the batched solver and the dot kernels
 constexpr int kWarps = kBlock / 32;
+// The single-system persistent solver runs one CTA of 24 warps per SM: one
+// exact partial record per SM keeps the grid-wide reduction short.
+constexpr int kSolveWarps = 24;
+constexpr int kSolveBlock = kSolveWarps * 32;
 
 struct KParams {
     int64_t n;

@@ -45,8 +45,10 @@ constexpr int kRec = 4;
 
 // Shared scratch of the block-level reductions: one exact accumulator per
 // slot and warp.
+template <int NW>
 struct XStage {
-    XAcc w[10][kWarps];
+    static_assert(NW >= 1 && NW <= 32, "one warp combines a slot");
+    XAcc w[10][NW];
 };
 
 template <class ACC>
@@ -71,9 +73,10 @@ __device__ __forceinline__ XAcc load_rec(const unsigned long long* r) {
 }
 
 // Sum the CTA's warp accumulators of the slots in MASK exactly and store them
-// as the CTA's record; slots in ZMASK are recorded as empty (zero).
-template <unsigned MASK, unsigned ZMASK = 0u, class ACC>
-__device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage& st, unsigned long long* rec) {
+// as the CTA's record; slots in ZMASK are recorded as empty (zero).  Warp
+// k mod NW combines slot k, so the slots are combined in parallel.
+template <unsigned MASK, unsigned ZMASK = 0u, int NW, class ACC>
+__device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage<NW>& st, unsigned long long* rec) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
@@ -83,12 +86,12 @@ __device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage& st, unsigne
         }
     }
     __syncthreads();
-    if (warp == 0) {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) {
+    for (int k = 0; k < 10; ++k) {
+        if (warp == k % NW) {
             if ((MASK >> k) & 1u) {
                 XAcc t;
-                if (lane < kWarps) t = st.w[k][lane]; else xa_init(t);
+                if (lane < NW) t = st.w[k][lane]; else xa_init(t);
                 t = xa_warp_aligned_sum(t);
                 if (lane == 0) store_rec(rec, k, t);
             } else if ((ZMASK >> k) & 1u) {
@@ -103,40 +106,47 @@ __device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage& st, unsigne
     __syncthreads();
 }
 
-// Pull this thread's share of the partial records into L1 ahead of use.
-__device__ __forceinline__ void prefetch_partials(const unsigned long long* base, int nblk) {
-    for (int c = threadIdx.x; c < nblk; c += kBlock) {
-        const char* r = (const char*)(base + (size_t)c * NSLOT * kRec);
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(r + 128));
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(r + 256));
-    }
-}
-
 // Sum every CTA's record exactly (all CTAs obtain the same values) and round
 // each slot once: out[k] = correctly rounded slot k, for the first NS slots.
-template <int NS = 10>
-__device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage& st, double* out) {
+// G = NW / NS warps share a slot; each lane loads its records in batches of
+// four (one memory round trip for up to 128 G records), merges them, and the
+// warp, then the slot's G warps, add their aligned partials.
+template <int NS, int NW>
+__device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage<NW>& st, double* out) {
+    static_assert(NS >= 1 && NS <= 10, "slots");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int G = NW >= NS ? NW / NS : 1;
+    constexpr int PASSES = NW >= NS ? 1 : (NS + NW - 1) / NW;
+    constexpr int kBatch = 4;
 #pragma unroll 1
-    for (int k = 0; k < NS; ++k) {
-        XAcc a;
-        xa_init(a);
-        for (int c = threadIdx.x; c < nblk; c += kBlock) {
-            xa_merge(a, load_rec(base + (size_t)c * NSLOT * kRec + k * kRec));
+    for (int pass = 0; pass < PASSES; ++pass) {
+        const int k = NW >= NS ? warp / G : warp + pass * NW;
+        const int g = NW >= NS ? warp % G : 0;
+        if (k < NS) {
+            XAcc a;
+            xa_init(a);
+            const unsigned long long* rk = base + k * kRec;
+            for (int c0 = g * 32 + lane; c0 < nblk; c0 += kBatch * G * 32) {
+                XAcc t[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int c = c0 + u * G * 32;
+                    if (c < nblk) t[u] = load_rec(rk + (size_t)c * NSLOT * kRec);
+                    else xa_init(t[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) xa_merge(a, t[u]);
+            }
+            a = xa_warp_aligned_sum(a);
+            if (lane == 0) st.w[k][g] = a;
         }
-        a = xa_warp_aligned_sum(a);
-        if (lane == 0) st.w[k][warp] = a;
     }
     __syncthreads();
-    if (warp == 0) {
-#pragma unroll 1
-        for (int k = 0; k < NS; ++k) {
-            XAcc t;
-            if (lane < kWarps) t = st.w[k][lane]; else xa_init(t);
-            t = xa_warp_aligned_sum(t);
-            if (lane == 0) out[k] = xa_round(t);
-        }
+    for (int k = warp; k < NS; k += NW) {
+        XAcc t;
+        if (lane < G) t = st.w[k][lane]; else xa_init(t);
+        t = xa_warp_aligned_sum(t);
+        if (lane == 0) out[k] = xa_round(t);
     }
     __syncthreads();
 }
@@ -159,19 +169,19 @@ struct ClusterGroup {
     }
 };
 
-template <class VT, class MT, int LAYOUT, int T, class Group>
+template <class VT, class MT, int LAYOUT, int T, int NW, class Group>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
-    __shared__ XStage s_x;
+    __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
     __shared__ double s_sc[4];
     __shared__ int s_ctl[2];
     __shared__ int s_flag;
-    __shared__ VT s_buf[kWarps][32];
-    __shared__ double s_buf64[kWarps][32];
+    __shared__ VT s_buf[NW][32];
+    __shared__ double s_buf64[NW][32];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t gwarp = (int64_t)grp.rank * kWarps + warp;
-    const int64_t nwarps = (int64_t)grp.size * kWarps;
+    const int64_t gwarp = (int64_t)grp.rank * NW + warp;
+    const int64_t nwarps = (int64_t)grp.size * NW;
     const int64_t n = P.n, ntiles = P.ntiles;
     const int nblk = grp.size;
     const int rank = grp.rank;
@@ -214,7 +224,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     WarpStager<VT> stg;
     stg.buf = (VT*)(s_dyn + (size_t)warp * 2 * kMaxStage * 32 * sizeof(VT));
-    stg.bar = (unsigned long long*)(s_dyn + (size_t)kWarps * 2 * kMaxStage * 32 * sizeof(VT)) + 2 * warp;
+    stg.bar = (unsigned long long*)(s_dyn + (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT)) + 2 * warp;
     stg.parity = 0u;
     stg.pending = 0u;
     stg.dead = false;
@@ -288,8 +298,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                                                                                                     myrec(0));
             flush_partials<(1u << ST)>(xt, s_x, myrec(0));
             if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
-            prefetch_partials(rbase(0), nblk);
-            reduce_partials(rbase(0), nblk, s_x, s_sum);
+            reduce_partials<10>(rbase(0), nblk, s_x, s_sum);
             const double rt2 = s_sum[ST];
             rtrue = sqrt(rt2);
             if (evals == 0) {
@@ -374,18 +383,16 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(cur));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
-                prefetch_partials(rbase(cur), nblk);
             } else {
-                // phase A: the partials of iteration i travel to L1 while A s_i of the
-                // first tile is computed (the overlap of the reduction with MV, Section 3)
-                prefetch_partials(rbase(cur), nblk);
+                // phase A: A s_i of the first tile is in flight while the partials of
+                // iteration i are reduced (the overlap of the reduction with MV, Section 3)
                 if (!rr_step) {
                     const VT* const vA0[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
                     stage_pro(vA0);
                     if (gwarp < ntiles) as_first = spmv(sCur, gwarp);
                 }
             }
-            reduce_partials(rbase(cur), nblk, s_x, s_sum);
+            reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
 
             // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
             if (threadIdx.x == 0) {
@@ -731,25 +738,25 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 }
 
 template <class VT, class MT, int LAYOUT, int T>
-__global__ void __launch_bounds__(kBlock, 3) solve_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
-    solve_body<VT, MT, LAYOUT, T>(P, grp);
+    solve_body<VT, MT, LAYOUT, T, kSolveWarps>(P, grp);
 }
 
 // dynamic shared memory of the solver kernels: the per-warp staging buffers and their mbarriers
-template <class VT>
+template <class VT, int NW>
 constexpr size_t stage_smem_bytes() {
-    return (size_t)kWarps * 2 * kMaxStage * 32 * sizeof(VT) + (size_t)kWarps * 2 * sizeof(unsigned long long);
+    return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT) + (size_t)NW * 2 * sizeof(unsigned long long);
 }
 
 template <class VT, class MT, int LAYOUT, int T>
 int launch_one(const KParams& P, int grid, cudaStream_t st) {
     void* args[] = {(void*)&P};
-    const size_t smem = stage_smem_bytes<VT>();
+    const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
     cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T>, dim3(grid), dim3(kBlock),
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T>, dim3(grid), dim3(kSolveBlock),
                                             args, smem, st);
 }
 
@@ -758,12 +765,12 @@ int max_grid_one(int* grid) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = stage_smem_bytes<VT>();
+    const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T>, kBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T>, kSolveBlock, smem);
     *grid = sms * per;
     return (int)e;
 }
@@ -844,7 +851,7 @@ __global__ void __launch_bounds__(kBlock) batched_kernel(const __grid_constant__
             sP.partials = B.partials + (size_t)cid * 2 * B.csize * NSLOT * kRec;
         }
         __syncthreads();
-        solve_body<VT, MT, LAY_CSR, T>(sP, grp);
+        solve_body<VT, MT, LAY_CSR, T, kWarps>(sP, grp);
     }
 }
 
@@ -857,13 +864,13 @@ int dispatch_batched(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = stage_smem_bytes<VT>();
+    cfg.dynamicSmemBytes = stage_smem_bytes<VT, kWarps>();
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void (*fn)(BatchArgs) = (tpr == 1) ? batched_kernel<VT, MT, 1> : batched_kernel<VT, MT, 8>;
     cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)stage_smem_bytes<VT>());
+                                         (int)stage_smem_bytes<VT, kWarps>());
     if (e == cudaSuccess && B->csize > 8)
         e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return (int)e;
