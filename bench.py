@@ -56,6 +56,8 @@ def args_parse():
     ap.add_argument("--cpu-iters", type=int, default=30, help="oracle iterations in the CPU sample")
     ap.add_argument("--size", type=int, default=128, help="grid side k of the k^3 system (128 = the benchmark)")
     ap.add_argument("--maxit", type=int, default=10000, help="iteration limit (smaller for profiling runs)")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the timed solves (no end-to-end, side-by-side or CPU legs): the command profiled by ncu")
     return ap.parse_args()
 
 
@@ -246,6 +248,14 @@ def main():
         per = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]
         return total_ms, per, results
 
+    if a.profile:
+        total_ms, per, results = run(a.kind, a.precision, a.steps, a.warmup)
+        r0 = results[-1]
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "kind": a.kind, "precision": a.precision, "layout": a.layout,
+                              "size": a.size, "iterations": r0["iterations"], "status": r0["status_name"],
+                              "kernel_ms": statistics.mean(per)}), flush=True)
+        return
     with Clocks(local) as ck:
         total_ms, per, results = run(a.kind, a.precision, a.steps, a.warmup)
     clocks = ck.summary()

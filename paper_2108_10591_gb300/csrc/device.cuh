@@ -287,6 +287,30 @@ __device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, c
     return acc;
 }
 
+// CSR tile, one lane per row, with the lane's row range [rp0, rp1) already
+// loaded (rows >= n: an empty range): the same entries, order and fmas as
+// csr_tile<VT, MT, 1>.
+template <class VT, class MT>
+__device__ __forceinline__ VT csr_tile_rp(int rp0, int rp1, const int32_t* __restrict__ col,
+                                          const MT* __restrict__ val, const VT* x) {
+    VT acc = VT(0);
+    for (int k0 = rp0; k0 < rp1; k0 += kSpmvBatch) {
+        int c[kSpmvBatch];
+        VT v[kSpmvBatch], xv[kSpmvBatch];
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j) {
+            const bool in = k0 + j < rp1;
+            c[j] = in ? __ldg(col + k0 + j) : 0;
+            v[j] = in ? (VT)ldv(val + k0 + j) : VT(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + j < rp1) ? x[c[j]] : VT(0);
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j)
+            if (k0 + j < rp1) acc = vfma(v[j], xv[j], acc);
+    }
+    return acc;
+}
 template <class VT, class MT, int LAYOUT, int T>
 __device__ __forceinline__ VT tile_spmv(const KParams& P, const MT* val, const VT* x, int64_t tile, VT* s_buf) {
     if constexpr (LAYOUT == LAY_SELL) {

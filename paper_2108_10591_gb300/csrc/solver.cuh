@@ -174,6 +174,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
     __shared__ double s_sc[4];
+    __shared__ double s_q[5];   // quotients and sqrt of the scalar recurrence
     __shared__ int s_ctl[2];
     __shared__ int s_flag;
     __shared__ VT s_buf[NW][32];
@@ -233,6 +234,20 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     constexpr long long kDrainBudget = 1000000000ll;
     // issue the warp's first two tiles of a phase (after the grid barrier that
     // made the previous phase's writes visible)
+    // CSR with one lane per row, FP32 vectors: the row range of the lane's row
+    // in the warp's next tile is loaded one tile ahead, so the SpMV of a tile
+    // starts with its column and value loads (in FP64 mode the two extra
+    // registers cost more than the latency they hide)
+    constexpr bool kRp = (LAYOUT == LAY_CSR && T == 1 && sizeof(VT) == 4);
+    auto rp_load = [&](int64_t t, int& a, int& b) {
+        a = 0; b = 0;
+        const int64_t r = t * 32 + lane;
+        if (t < ntiles && r < n) { a = __ldg(P.rowptr + r); b = __ldg(P.rowptr + r + 1); }
+    };
+    auto spmv_rp = [&](const VT* xv, int64_t tile, int a, int b) -> VT {
+        if constexpr (kRp) return csr_tile_rp<VT, MT>(a, b, P.col, val, xv);
+        else return spmv(xv, tile);
+    };
     auto stage_pro = [&](const auto& v) {
         if (gwarp < ntiles) stg.issue(v, gwarp, 0);
         if (gwarp + nwarps < ntiles) stg.issue(v, gwarp + nwarps, 1);
@@ -355,8 +370,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_init10(xv);
                 const VT* const vPA[] = {Y, R, RS};
                 stage_pro(vPA);
+                int rpa = 0, rpb = 0;
+                if (kRp) rp_load(gwarp, rpa, rpb);
                 for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
-                    const VT sv = spmv(R, tile);
+                    int rpa_n = 0, rpb_n = 0;
+                    if (kRp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    const VT sv = spmv_rp(R, tile, rpa, rpb);
+                    rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
@@ -395,32 +415,57 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
 
             // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
-            if (threadIdx.x == 0) {
+            // The independent quotients are formed side by side by the lanes of
+            // warp 0 (one division sequence) while warp 1 takes the square root;
+            // thread 0 then finishes alpha and the bookkeeping.  Every value is
+            // the same IEEE quotient of the same operands as in a sequential
+            // evaluation.
+            if (warp == 0 && lane < 4) {
                 const double a = s_sum[SA], bb = s_sum[SB], c = s_sum[SC], d = s_sum[SD], e = s_sum[SE];
+                const double f = s_sum[SF], g = s_sum[SG];
+                const double den = a * bb - c * c;
+                double num = d, dv = a;  // lane 3: d / a
+                if (lane == 0) {
+                    num = i == 0 ? f : alpha_p * f;
+                    dv = i == 0 ? g : zeta_p * f_p;
+                } else if (lane == 1) {
+                    num = bb * d - c * e;
+                    dv = den;
+                } else if (lane == 2) {
+                    num = a * e - c * d;
+                    dv = den;
+                }
+                s_q[lane] = num / dv;
+            } else if (warp == 1 && lane == 0) {
+                s_q[4] = sqrt(s_sum[SR]);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const double a = s_sum[SA], bb = s_sum[SB], c = s_sum[SC];
                 const double f = s_sum[SF], g = s_sum[SG], h = s_sum[SH], rr = s_sum[SR];
                 double alpha, beta, zeta, eta;
                 bool brk;
                 if (i == 0) {
                     beta = 0.0;
-                    alpha = f / g;
-                    zeta = d / a;
+                    alpha = s_q[0];   // f / g
+                    zeta = s_q[3];    // d / a
                     eta = 0.0;
                     brk = (g == 0.0 || a == 0.0);
                 } else {
-                    beta = (alpha_p * f) / (zeta_p * f_p);
+                    beta = s_q[0];    // (alpha_{i-1} f_i) / (zeta_{i-1} f_{i-1})
                     alpha = f / (g + beta * h);
                     const double den = a * bb - c * c;
                     if (den == 0.0 || !isfinite(den)) {
-                        zeta = d / a;
+                        zeta = s_q[3];
                         eta = 0.0;
                         ++fallbacks;
                     } else {
-                        zeta = (bb * d - c * e) / den;
-                        eta = (a * e - c * d) / den;
+                        zeta = s_q[1];
+                        eta = s_q[2];
                     }
                     brk = (zeta_p * f_p == 0.0 || g + beta * h == 0.0 || a == 0.0);
                 }
-                const double rn = sqrt(rr);
+                const double rn = s_q[4];
                 const bool conv = rn <= thr_in;
                 if (i == 0 || rn < best_rn) { best_rn = rn; since_best = 0; } else { ++since_best; }
                 int dec = 0, st = BCS_OK;
@@ -483,8 +528,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_init10(xv);
                 const VT* const vPC[] = {O, R, U, sCur, Y, Pv, RS, Z};
                 stage_pro(vPC);
+                int rpa = 0, rpb = 0;
+                if (kRp) rp_load(gwarp, rpa, rpb);
                 for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
-                    const VT w = spmv(U, tile);
+                    int rpa_n = 0, rpb_n = 0;
+                    if (kRp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    const VT w = spmv_rp(U, tile, rpa, rpb);
+                    rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
@@ -526,8 +576,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase A (continued): fused recurrences of Alg. 4
                 wa_init10(xv);
                 const VT* const vA[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
+                int rpa = 0, rpb = 0;
+                if (kRp) rp_load(gwarp + nwarps, rpa, rpb);
                 for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
-                    const VT As = (tile == gwarp) ? as_first : spmv(sCur, tile);
+                    int rpa_n = 0, rpb_n = 0;
+                    if (kRp && tile > gwarp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    const VT As = (tile == gwarp) ? as_first : spmv_rp(sCur, tile, rpa, rpb);
+                    if (tile > gwarp) { rpa = rpa_n; rpb = rpb_n; }
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
@@ -578,8 +633,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_init10(xv);
                 const VT* const vC[] = {L, G, sNxt, Y, R, RS};
                 stage_pro(vC);
+                rpa = 0; rpb = 0;
+                if (kRp) rp_load(gwarp, rpa, rpb);
                 for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
-                    const VT Aw = spmv(W, tile);
+                    int rpa_n = 0, rpb_n = 0;
+                    if (kRp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    const VT Aw = spmv_rp(W, tile, rpa, rpb);
+                    rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);

@@ -253,14 +253,18 @@ __device__ __forceinline__ void wa_add_term(WAcc& a, unsigned long long ph, unsi
                                             bool valid, bool special) {
     if (__any_sync(0xffffffffu, special)) a.eb = kXaNaN;
     if (a.eb == kXaNaN) return;
-    const int wmax = warp_max_int(valid ? pe + kWaTop : kWaNone);
-    if (wmax == kWaNone) return;
-    if (a.eb == kXaEmpty) {
-        a.eb = wmax - kWaTop;
-    } else if (wmax > a.eb + kWaTop) {
-        const int d = wmax - kWaTop - a.eb;
-        sar128(a.hi, a.lo, d);
-        a.eb += d;
+    const int top = valid ? pe + kWaTop : kWaNone;
+    // the window moves only when some lane's term ends above it (one vote in
+    // the common case; the warp maximum only when it has to move)
+    if (!__all_sync(0xffffffffu, top <= a.eb + kWaTop)) {
+        const int wmax = warp_max_int(top);
+        if (a.eb == kXaEmpty) {
+            a.eb = wmax - kWaTop;
+        } else {
+            const int d = wmax - kWaTop - a.eb;
+            sar128(a.hi, a.lo, d);
+            a.eb += d;
+        }
     }
     shr128(ph, pl, a.eb - pe);
     if (!valid) {
@@ -384,7 +388,10 @@ __device__ __forceinline__ void wa_acc(DAcc& a, float x, float y, bool valid) {
     if (valid) a.s = fma(widen(x), widen(y), a.s);
 }
 
-// exact 192-bit representation of a double
+// exact 192-bit representation of a double, its significand placed at bits
+// 70..122 so that aligning it to a partial up to 2^70 times larger keeps
+// every bit (the merges then do not depend on how lanes are grouped)
+constexpr int kXaDblShift = 70;
 __device__ __forceinline__ XAcc xa_from_double(double d) {
     XAcc r;
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
@@ -399,12 +406,18 @@ __device__ __forceinline__ XAcc xa_from_double(double d) {
         r.e = kXaEmpty;
         return r;
     }
-    r.e = E ? E - 1075 : -1074;
-    r.w0 = m;
+    r.e = (E ? E - 1075 : -1074) - kXaDblShift;
+    static_assert(kXaDblShift >= 64 && kXaDblShift + 53 <= 127, "significand inside w1");
+    r.w1 = m << (kXaDblShift - 64);
     if (b >> 63) {  // negate
-        r.w0 = ~r.w0 + 1ull;
-        r.w1 = ~0ull;
+        r.w0 = ~r.w0;
+        r.w1 = ~r.w1;
         r.w2 = ~0ull;
+        r.w0 += 1ull;
+        if (r.w0 == 0ull) {
+            r.w1 += 1ull;
+            if (r.w1 == 0ull) r.w2 += 1ull;
+        }
     }
     return r;
 }
