@@ -13,6 +13,8 @@ copies inside the timed region).  Prints one JSON line on rank 0.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -32,6 +34,28 @@ HBM_PEAK_FALLBACK = 6800.0
 SMS = 152
 DFMA_PER_CLK_SM = 2          # GB300: FP64 FMA issue rate per SM per clock
 SM_MAX_MHZ = 2070.0
+
+
+# DRAM traffic of the solve kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on this
+# workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
+# iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
+# for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
+TRAFFIC = {"fp64": {"per_iter": 929.4e6, "per_outer": 1013.2e6},
+           "fp32": {"per_iter": 525.0e6, "per_outer": 822.8e6}}
+KERNEL_SHA = "be25a675e106046f"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2108_10591_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_2108_10591_gb300", "csrc", "*.cuh")) +
+                   glob.glob(os.path.join(ROOT, "paper_2108_10591_gb300", "csrc", "*.h")) +
+                   [os.path.join(ROOT, "include", "bcs.h")])
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -271,17 +295,31 @@ def main():
 
     # roofline of the solve kernel (the only kernel in the step)
     peaks, peak_src = measured_peaks()
-    f, by = solve_work(a.kind, n, nnz, iters, outer)
+    lo = a.precision != "fp64"
+    vb, mb = (4, 4 if a.precision == "fp32" else 2) if lo else (8, 8)
+    f, by = solve_work(a.kind, n, nnz, iters, outer, vb, mb)
     fp64_peak = SMS * DFMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6
     achieved_tf = f / (kernel_ms * 1e-3) / 1e12
     achieved_gbs = by / (kernel_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved_tf / (fp64_peak / 1e12), "traffic": None,
-                "kernel": "solve_kernel<double,double,CSR>", "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 "
-                "flop x 2070 MHz (FP64 ALU; the kernel's binding unit on GB300)",
-                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                        "peak_source": peak_src}}
+    traffic = None
+    tr = TRAFFIC.get(a.precision)
+    if (tr and a.kind == "p-BiCGSafe" and a.layout == "csr" and a.size == 128 and a.tpr in (0, 1)
+            and kernel_sources_sha() == KERNEL_SHA):
+        traffic = tr["per_iter"] * iters + tr["per_outer"] * outer
+    kname = "solve_kernel<%s,%s,%s>" % ("float" if lo else "double",
+                                        {"fp64": "double", "fp32": "float", "bf16": "bf16"}[a.precision],
+                                        a.layout.upper())
+    hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+           "peak_source": peak_src}
+    if lo:
+        # FP32/BF16 vectors: the FP64 units only accumulate the inner products; HBM bounds the kernel
+        roofline = dict(bound="hbm", traffic=traffic, kernel=kname, **hbm)
+    else:
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved_tf / (fp64_peak / 1e12), "traffic": traffic,
+                    "kernel": kname, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 "
+                    "flop x 2070 MHz (FP64 ALU; the kernel's binding unit on GB300)", "hbm": hbm}
 
     # end to end through the public API with host buffers
     bh = torch.from_numpy(b).pin_memory().numpy()
@@ -324,10 +362,11 @@ def main():
                              "scaled to one solve by the GPU solve's %d iterations" % (a.cpu_iters, a.kind, dt, iters)}
         line = {"metric": METRIC, "value": world * 1e3 / ms_per_step, "unit": "solves/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[a.precision], "data": "synthetic",
                 "config": {"workload": "cd3d_%d: 3D -Lap u + 50(u_x+u_y+u_z), %d^3, 7-point upwind, n=%d, nnz=%d, "
                                        "b=A*1, x0=0" % (a.size, a.size, n, nnz),
-                           "kind": a.kind, "precision": "fp64", "layout": a.layout, "tol": 1e-10,
+                           "kind": a.kind, "precision": a.precision, "layout": a.layout, "tol": 1e-10,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "no flush: matrix (183 MB) and vectors (16 x 16.8 MB) exceed the 129 MB L2"},
                 "iterations": iters, "outer_steps": outer, "converged_all_steps": ok,
