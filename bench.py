@@ -58,6 +58,31 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
+# Side workloads (the other synthetic configurations): one JSON line each, not the benchmark line.
+SIDE_WORKLOADS = {
+    "powerlaw_4m": "random nonsymmetric, n=4,194,304, power-law rows (exponent 2.1, mean 16, max 512), 90% of columns "
+                   "within n/100 of the diagonal, N(0,1) values, diagonal 1.2 x row abs-sum",
+    "cd3d27_192": "3D 27-point convection-diffusion, 192^3 (n=7,077,888), beta=100 on the face couplings",
+    "batch_cd2d_512": "512 independent 2D 5-point convection-diffusion systems, side U{32..256}, beta U[0,50]",
+}
+
+
+def shard_systems(nsys, rank, world):
+    """Systems of a batch taken by one rank (weak scaling, no collective): every world-th system
+    of the list in decreasing size, so that the ranks' shares have about equal work."""
+    return list(range(rank, nsys, world))
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """Largest value over the ranks (the slowest rank's time); the value itself on one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -80,6 +105,9 @@ def args_parse():
     ap.add_argument("--cpu-iters", type=int, default=30, help="oracle iterations in the CPU sample")
     ap.add_argument("--size", type=int, default=128, help="grid side k of the k^3 system (128 = the benchmark)")
     ap.add_argument("--maxit", type=int, default=10000, help="iteration limit (smaller for profiling runs)")
+    ap.add_argument("--workload", default="cd3d_128", choices=list(SIDE_WORKLOADS) + ["cd3d_128"],
+                    help="cd3d_128 (the benchmark line); the others print a side measurement line")
+    ap.add_argument("--tune", action="store_true", help="side workloads: autotune the layout / lanes per row first")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed solves (no end-to-end, side-by-side or CPU legs): the command profiled by ncu")
     return ap.parse_args()
@@ -210,6 +238,93 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
+# ---- side workloads --------------------------------------------------------------------------
+
+def side_single(a, bcs, torch, dist, world, rank):
+    import workloads as W
+    A = W.powerlaw() if a.workload == "powerlaw_4m" else W.cd3d27(192, 100.0)
+    b = W.rhs_ones(A)
+    layouts = bcs.LAYOUT_CSR | bcs.LAYOUT_SELL
+    M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    tune = None
+    if a.tune:
+        best, cands = bcs.autotune(M, a.kind, precision=a.precision, iters=20)
+        tune = {"best": best, "candidates": cands}
+        layout, tpr = "auto", 0
+    else:
+        layout, tpr = a.layout, a.tpr
+    S = bcs.solver_create(M, a.kind, tol=1e-10, maxit=a.maxit, precision=a.precision, layout=layout,
+                          threads_per_row=tpr, max_outer=30)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    for _ in range(a.warmup):
+        xd.zero_()
+        bcs.solve(S, bd, xd)
+    times, res = [], None
+    for _ in range(a.steps):
+        xd.zero_()
+        res = bcs.solve(S, bd, xd)
+        times.append(res["seconds"])
+    t = max_over_ranks(statistics.mean(times), dist, "cuda")
+    lo = a.precision != "fp64"
+    vb, mb = (4, 4 if a.precision == "fp32" else 2) if lo else (8, 8)
+    _, by = solve_work(a.kind, A.n, A.nnz, res["iterations"], res["outer_steps"], vb, mb)
+    peaks, src = measured_peaks()
+    gbs = by / t / 1e9
+    hp = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    return {"metric": "time to 1e-10 rel. residual", "value": world / t, "unit": "solves/s", "n_gpus": world,
+            "ms_per_solve": t * 1e3, "iterations": res["iterations"], "outer_steps": res["outer_steps"],
+            "us_per_iter": t * 1e6 / max(1, res["iterations"]), "status": res["status_name"],
+            "rel_res_true": res["rel_res_true"],
+            "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "n": A.n, "nnz": A.nnz,
+                       "kind": a.kind, "precision": a.precision, "layout": layout, "threads_per_row": tpr},
+            "hbm": {"achieved": gbs, "peak": hp, "unit": "GB/s", "frac": gbs / hp, "peak_source": src},
+            "tune": tune}
+
+
+def side_batch(a, bcs, torch, dist, world, rank):
+    import workloads as W
+    mats, sides, betas = W.batch_cd2d(512)
+    order = sorted(range(len(mats)), key=lambda k: -(mats[k].nnz + mats[k].n))
+    mine = [order[k] for k in shard_systems(len(order), rank, world)]
+    mats = [mats[k] for k in mine]
+    Ms = [bcs.csr_upload(A, stores=bcs.STORE_F32) for A in mats]
+    kw = dict(precision=a.precision, max_outer=30)
+    if a.kind == "p-BiCGSafe-rr":
+        kw["rr_m"] = 20
+    tune = None
+    if a.tune:
+        kw, cands = bcs.batch_autotune(Ms, kind=a.kind, iters=20, **kw)
+        tune = {"options": {"threads_per_row": kw["threads_per_row"], "ctas_per_sm": kw["ctas_per_sm"]},
+                "candidates": cands}
+    bt = bcs.Batch(Ms, kind=a.kind, tol=1e-10, maxit=a.maxit, **kw)
+    offs = np.cumsum([0] + [A.n for A in mats])
+    bflat = torch.from_numpy(np.concatenate([W.rhs_ones(A) for A in mats])).cuda()
+    xflat = torch.zeros_like(bflat)
+    bs = [bflat[offs[k]:offs[k + 1]] for k in range(len(mats))]
+    xs = [xflat[offs[k]:offs[k + 1]] for k in range(len(mats))]
+    for _ in range(a.warmup):
+        xflat.zero_()
+        bt.solve(bs, xs)
+    times, res, code = [], None, 0
+    for _ in range(a.steps):
+        xflat.zero_()
+        code, res = bt.solve(bs, xs)
+        times.append(res[0]["seconds"])
+    t = max_over_ranks(statistics.mean(times), dist, "cuda")
+    its = [r["iterations"] for r in res]
+    ok = sum(1 for r in res if r["status"] == 0)
+    return {"metric": "solves/s", "value": 512 / t, "unit": "solves/s", "n_gpus": world, "ms_per_batch": t * 1e3,
+            "systems": 512, "systems_this_rank": len(mats), "converged_this_rank": ok, "worst_status": code,
+            "iterations": {"min": min(its), "median": float(np.median(its)), "max": max(its)},
+            "max_rel_res_true": max(r["rel_res_true"] for r in res),
+            "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "kind": a.kind,
+                       "precision": a.precision, "batch_options": {k: kw[k] for k in kw
+                                                                    if k in ("threads_per_row", "ctas_per_sm")},
+                       "parallelism": "systems sharded over ranks" if world > 1 else "single GPU"},
+            "tune": tune}
+
+
 # ---- our arm ---------------------------------------------------------------------------------
 
 def main():
@@ -228,6 +343,18 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     import paper_2108_10591_gb300 as bcs
+
+    if a.workload != "cd3d_128":
+        fn = side_batch if a.workload == "batch_cd2d_512" else side_single
+        line = fn(a, bcs, torch, dist, world, rank)
+        if rank == 0:
+            line["data"] = "synthetic"
+            line["side_measurement"] = True
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     A, b = make_workload(a.size)
     n, nnz = A.n, A.nnz

@@ -37,6 +37,7 @@ extern "C" {
 
 typedef struct bcs_matrix_s* bcs_matrix;
 typedef struct bcs_solver_s* bcs_solver;
+typedef struct bcs_batch_s* bcs_batch;
 
 /* Methods (the paper's Algorithms 3, 4 and 5). */
 enum { BCS_SSBICGSAFE2 = 0, BCS_P_BICGSAFE = 1, BCS_P_BICGSAFE_RR = 2 };
@@ -49,8 +50,10 @@ enum { BCS_SSBICGSAFE2 = 0, BCS_P_BICGSAFE = 1, BCS_P_BICGSAFE_RR = 2 };
  * The paper has no counterpart of the two refinement modes. */
 enum { BCS_FP64 = 0, BCS_FP32_REFINE = 1, BCS_BF16MAT_REFINE = 2 };
 
-/* Matrix layouts held on the device (bit mask for bcs_csr_upload). */
-enum { BCS_LAYOUT_CSR = 1, BCS_LAYOUT_SELL = 2 };
+/* Matrix layouts held on the device (bit mask for bcs_csr_upload).
+ * BCS_LAYOUT_AUTO (solver option only): the layout bcs_autotune chose for the
+ * matrix and precision, CSR if it was not tuned. */
+enum { BCS_LAYOUT_AUTO = 0, BCS_LAYOUT_CSR = 1, BCS_LAYOUT_SELL = 2 };
 /* Value copies held on the device (bit mask; FP64 is always kept). */
 enum { BCS_STORE_F64 = 1, BCS_STORE_F32 = 2, BCS_STORE_BF16 = 4 };
 
@@ -73,9 +76,12 @@ typedef struct {
     double inner_tol;     /* refinement modes: inner stop at ||r_inner|| <= inner_tol*||r_outer|| (default 1e-3) */
     int max_outer;        /* outer steps: true-residual checks / restarts / refinement steps (default 30) */
     int history_len;      /* capacity of the residual history (default 4096 entries) */
-    int layout;           /* BCS_LAYOUT_CSR (default) or BCS_LAYOUT_SELL; must have been uploaded */
-    int threads_per_row;  /* CSR only: 1, 4, 8 or 32 lanes per row; 0 = the library's choice (1) */
-    int ctas_per_sm;      /* 0 = chosen by occupancy; otherwise 1..8 */
+    int layout;           /* BCS_LAYOUT_AUTO (default: tuned, else CSR), BCS_LAYOUT_CSR or BCS_LAYOUT_SELL
+                             (must have been uploaded) */
+    int threads_per_row;  /* CSR only: 1, 4, 8 or 32 lanes per row; 0 = the library's choice (the tuned
+                             value, else 1) */
+    int ctas_per_sm;      /* single system: CTAs per SM, 0 = by occupancy (one 24-warp CTA); batched
+                             solves: CTAs per cluster (one cluster per system), 0 = 2; 1..8 */
     int max_ctas;         /* 0 = no cap; otherwise an upper bound on the grid size */
     double spin_budget_ms;/* per grid-barrier wait before BCS_ERR_TIMEOUT (default 2000 ms) */
     int inner_maxit;      /* refinement modes: at most this many iterations per inner run (0 = no cap) */
@@ -244,6 +250,60 @@ void bcs_solver_destroy(bcs_solver s);
 int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int maxit,
                       const bcs_options* opt, const double* const* b, double* const* x,
                       bcs_result* res, void* stream);
+
+/*
+ * Reusable batched solve (no counterpart in the paper).  bcs_batch_create
+ * validates the nsys matrices and options exactly as bcs_solve_batched,
+ * allocates the workspace once and fixes the work order (largest systems
+ * first); bcs_batch_solve then solves the same systems for new right-hand
+ * sides: b[k], x[k] as for bcs_solve_batched (x[k] in: x0, out: solution).
+ * The first solve captures the launch sequence (parameter upload, counter
+ * resets, the persistent kernel, result download) in a CUDA graph that later
+ * solves replay; if capture is not possible the sequence is issued directly.
+ * bcs_batch_solve synchronises the stream and returns the worst status; a
+ * handle is not thread-safe and runs one solve at a time.  The matrices must
+ * outlive the handle.  bcs_batch_destroy(NULL) is ignored.
+ * Errors: BCS_ERR_ARG (invalid arguments), BCS_ERR_OOM, BCS_ERR_CUDA.
+ */
+int bcs_batch_create(int nsys, const bcs_matrix* A, int kind, double tol, int maxit,
+                     const bcs_options* opt, bcs_batch* out);
+int bcs_batch_solve(bcs_batch bt, const double* const* b, double* const* x, bcs_result* res, void* stream);
+void bcs_batch_destroy(bcs_batch bt);
+
+/* One measured candidate of the autotuner. */
+typedef struct {
+    int layout;            /* BCS_LAYOUT_CSR or BCS_LAYOUT_SELL */
+    int threads_per_row;   /* CSR lanes per row (1 for SELL) */
+    int cluster_ctas;      /* batched: CTAs per cluster; 0 for single-system candidates */
+    double us_per_iter;    /* device time per iteration (single system) or per batch iteration */
+} bcs_tune_entry;
+
+/*
+ * Autotuner (no counterpart in the paper).  Times `iters` iterations (0 = 20)
+ * of the persistent solver of method `kind` in `precision` (tolerance 0, one
+ * run, b = ones, x0 = 0) for every candidate the matrix supports: CSR with 1,
+ * 4, 8 and 32 lanes per row, and SELL-C-sigma if uploaded; each candidate
+ * is run twice and the second run timed.  The fastest is recorded in A for
+ * that precision: solvers created later with layout BCS_LAYOUT_AUTO and
+ * threads_per_row 0 use it, and bcs_spmv uses its lanes per row.
+ *   entries   host array of cap entries (may be NULL): the measurements,
+ *             in candidate order; *count (may be NULL) the number of candidates.
+ *   best      (may be NULL) the chosen candidate.
+ * Synchronises the stream.  Errors: BCS_ERR_ARG, BCS_ERR_OOM, BCS_ERR_CUDA.
+ */
+int bcs_autotune(bcs_matrix A, int kind, int precision, int iters, bcs_tune_entry* entries, int cap,
+                 int* count, bcs_tune_entry* best, void* stream);
+
+/*
+ * Batched autotuner: times `iters` iterations (0 = 20) per system of the
+ * batched solve of the nsys systems for CSR lanes per row 1 and 8 and
+ * clusters of 1, 2, 4 and 8 CTAs, with the other settings taken from opt
+ * (may be NULL).  *best_opt (required) receives opt with the fastest
+ * threads_per_row and ctas_per_sm (CTAs per cluster) filled in, ready for
+ * bcs_batch_create.  entries, cap, count as for bcs_autotune.
+ */
+int bcs_batch_autotune(int nsys, const bcs_matrix* A, int kind, const bcs_options* opt, int iters,
+                       bcs_tune_entry* entries, int cap, int* count, bcs_options* best_opt, void* stream);
 
 /* Static English name of a status code. */
 const char* bcs_status_string(int status);

@@ -21,13 +21,14 @@ SSBICGSAFE2, P_BICGSAFE, P_BICGSAFE_RR = 0, 1, 2
 KINDS = {"ssBiCGSafe2": SSBICGSAFE2, "p-BiCGSafe": P_BICGSAFE, "p-BiCGSafe-rr": P_BICGSAFE_RR}
 FP64, FP32_REFINE, BF16MAT_REFINE = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32_REFINE, "bf16": BF16MAT_REFINE}
-LAYOUT_CSR, LAYOUT_SELL = 1, 2
+LAYOUT_AUTO, LAYOUT_CSR, LAYOUT_SELL = 0, 1, 2
 STORE_F64, STORE_F32, STORE_BF16 = 1, 2, 4
 OK, NOT_CONVERGED, ERR_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NONFINITE, ERR_OOM = 0, 1, -1, -2, -3, -4, -5, -6
 
 EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv", "bcs_dot", "bcs_dot_noalloc",
             "bcs_matrix_free", "bcs_solver_create", "bcs_solve", "bcs_solve_host", "bcs_get_history",
-            "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_status_string"]
+            "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_batch_create", "bcs_batch_solve",
+            "bcs_batch_destroy", "bcs_autotune", "bcs_batch_autotune", "bcs_status_string"]
 
 
 class Options(ctypes.Structure):
@@ -47,6 +48,14 @@ class Result(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["status_name"] = status_string(self.status)
         return d
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("cluster_ctas", ctypes.c_int),
+                ("us_per_iter", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def _load():
@@ -74,6 +83,13 @@ def _load():
     L.bcs_solver_destroy.argtypes = [P]
     L.bcs_solver_destroy.restype = None
     L.bcs_solve_batched.argtypes = [I, P, I, D, I, ctypes.POINTER(Options), P, P, P, P]
+    L.bcs_batch_create.argtypes = [I, P, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
+    L.bcs_batch_solve.argtypes = [P, P, P, P, P]
+    L.bcs_batch_destroy.argtypes = [P]
+    L.bcs_batch_destroy.restype = None
+    L.bcs_autotune.argtypes = [P, I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(TuneEntry), P]
+    L.bcs_batch_autotune.argtypes = [I, P, I, ctypes.POINTER(Options), I, P, I, ctypes.POINTER(I),
+                                     ctypes.POINTER(Options), P]
     L.bcs_status_string.argtypes = [I]
     L.bcs_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -119,6 +135,10 @@ def _stream(stream):
     return stream if isinstance(stream, int) else stream.cuda_stream
 
 
+def _precision(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
 def options(**kw):
     o = Options()
     lib.bcs_options_default(ctypes.byref(o))
@@ -126,7 +146,7 @@ def options(**kw):
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
         if k == "layout" and isinstance(v, str):
-            v = {"csr": LAYOUT_CSR, "sell": LAYOUT_SELL}[v]
+            v = {"auto": LAYOUT_AUTO, "csr": LAYOUT_CSR, "sell": LAYOUT_SELL}[v]
         setattr(o, k, v)
     return o
 
@@ -300,3 +320,68 @@ def solve_batched(Ms, bs, xs, kind="p-BiCGSafe", tol=1e-10, maxit=10000, stream=
     if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
         raise BcsError(code, "bcs_solve_batched")
     return code, [R[i].as_dict() for i in range(n)]
+
+
+class Batch:
+    """Reusable batched solve (bcs_batch): the systems are fixed at creation,
+    every solve takes new device vectors b[k], x[k]."""
+
+    def __init__(self, Ms, kind="p-BiCGSafe", tol=1e-10, maxit=10000, **kw):
+        self.Ms = list(Ms)  # keeps the matrices alive
+        self.handle = None
+        n = len(self.Ms)
+        opts = options(**kw)
+        H = (ctypes.c_void_p * n)(*[m.handle for m in self.Ms])
+        h = ctypes.c_void_p()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(lib.bcs_batch_create(n, ctypes.cast(H, ctypes.c_void_p), k, float(tol), int(maxit), ctypes.byref(opts),
+                                    ctypes.byref(h)), "bcs_batch_create")
+        self.handle = h.value
+
+    def solve(self, bs, xs, stream=None):
+        """Returns (worst status, list of result dicts)."""
+        n = len(self.Ms)
+        if len(bs) != n or len(xs) != n:
+            raise ValueError("one b and one x per system")
+        B = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+        X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+        R = (Result * n)()
+        code = lib.bcs_batch_solve(self.handle, ctypes.cast(B, ctypes.c_void_p), ctypes.cast(X, ctypes.c_void_p),
+                                   ctypes.cast(R, ctypes.c_void_p), _stream(stream))
+        if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
+            raise BcsError(code, "bcs_batch_solve")
+        return code, [R[i].as_dict() for i in range(n)]
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.bcs_batch_destroy(self.handle)
+            self.handle = None
+
+
+def autotune(M, kind="p-BiCGSafe", precision="fp64", iters=20, stream=None):
+    """bcs_autotune: times every layout / lanes-per-row candidate of the persistent solver on M and
+    records the fastest in M for that precision.  Returns (best, list of measured candidates)."""
+    E = (TuneEntry * 8)()
+    cnt = ctypes.c_int()
+    best = TuneEntry()
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib.bcs_autotune(M.handle, k, _precision(precision), int(iters), ctypes.cast(E, ctypes.c_void_p), 8,
+                            ctypes.byref(cnt), ctypes.byref(best), _stream(stream)), "bcs_autotune")
+    return best.as_dict(), [E[i].as_dict() for i in range(min(cnt.value, 8))]
+
+
+def batch_autotune(Ms, kind="p-BiCGSafe", iters=20, stream=None, **kw):
+    """bcs_batch_autotune: returns (keyword options for Batch / solve_batched, measured candidates)."""
+    n = len(Ms)
+    H = (ctypes.c_void_p * n)(*[m.handle for m in Ms])
+    opts = options(**kw)
+    out = Options()
+    E = (TuneEntry * 16)()
+    cnt = ctypes.c_int()
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib.bcs_batch_autotune(n, ctypes.cast(H, ctypes.c_void_p), k, ctypes.byref(opts), int(iters),
+                                  ctypes.cast(E, ctypes.c_void_p), 16, ctypes.byref(cnt), ctypes.byref(out),
+                                  _stream(stream)), "bcs_batch_autotune")
+    best = dict(kw)
+    best.update(threads_per_row=out.threads_per_row, ctas_per_sm=out.ctas_per_sm)
+    return best, [E[i].as_dict() for i in range(min(cnt.value, 16))]

@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <numeric>
 #include <vector>
 
@@ -21,7 +22,7 @@ BCS_DECL(bf16)
 int dispatch_batched_f64(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
 int dispatch_batched_f32(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
 int dispatch_batched_bf16(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
-int default_tpr(const bcs_matrix_s* A);
+int default_tpr(const bcs_matrix_s* A, int precision);
 }  // namespace bcs
 
 namespace {
@@ -73,8 +74,9 @@ const void* inner_values(bcs_matrix A, int layout, int valtype) {
 
 int check_options(const bcs_options& o) {
     if (o.rr_m <= 0 || o.rr_M < 0 || o.max_outer <= 0 || o.history_len < 0) return BCS_ERR_ARG;
+    if (o.precision < BCS_FP64 || o.precision > BCS_BF16MAT_REFINE) return BCS_ERR_ARG;
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return BCS_ERR_ARG;
-    if (o.layout != BCS_LAYOUT_CSR && o.layout != BCS_LAYOUT_SELL) return BCS_ERR_ARG;
+    if (o.layout != BCS_LAYOUT_AUTO && o.layout != BCS_LAYOUT_CSR && o.layout != BCS_LAYOUT_SELL) return BCS_ERR_ARG;
     if (o.threads_per_row != 0 && !valid_tpr(o.threads_per_row)) return BCS_ERR_ARG;
     if (o.ctas_per_sm < 0 || o.ctas_per_sm > 8 || o.max_ctas < 0) return BCS_ERR_ARG;
     if (!(o.spin_budget_ms > 0.0)) return BCS_ERR_ARG;
@@ -95,7 +97,7 @@ void bcs_options_default(bcs_options* o) {
     o->inner_tol = 1e-3;
     o->max_outer = 30;
     o->history_len = 4096;
-    o->layout = BCS_LAYOUT_CSR;
+    o->layout = BCS_LAYOUT_AUTO;
     o->threads_per_row = 0;
     o->ctas_per_sm = 0;
     o->max_ctas = 0;
@@ -139,6 +141,10 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (o.rr_M == 0) o.rr_M = maxit + 1;
     int rc = check_options(o);
     if (rc) return rc;
+    if (o.layout == BCS_LAYOUT_AUTO) {
+        const int tl = A->tuned_layout[o.precision];
+        o.layout = (tl && (A->layouts & tl)) ? tl : BCS_LAYOUT_CSR;
+    }
     if (!(A->layouts & o.layout)) return BCS_ERR_ARG;
     bcs_solver s = new bcs_solver_s();
     s->A = A;
@@ -149,7 +155,7 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     rc = precision_types(A, o.precision, &s->vt_f32, &s->valtype);
     if (rc) { delete s; return rc; }
     s->layout = o.layout == BCS_LAYOUT_SELL ? LAY_SELL : LAY_CSR;
-    s->tpr = s->layout == LAY_SELL ? 1 : (o.threads_per_row ? o.threads_per_row : default_tpr(A));
+    s->tpr = s->layout == LAY_SELL ? 1 : (o.threads_per_row ? o.threads_per_row : default_tpr(A, o.precision));
     s->vbytes = s->vt_f32 ? sizeof(float) : sizeof(double);
     const int64_t n = A->n, nn = std::max<int64_t>(n, 1);
     const int64_t ntiles = (n + 31) / 32;
@@ -334,11 +340,11 @@ int bcs_get_scalars(bcs_solver s, double* out, int cap, int* len) {
     return BCS_OK;
 }
 
-int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int maxit, const bcs_options* opt,
-                      const double* const* b, double* const* x, bcs_result* res, void* stream) {
-    if (nsys < 0 || (nsys > 0 && (!A || !b || !x))) return BCS_ERR_ARG;
+int bcs_batch_create(int nsys, const bcs_matrix* A, int kind, double tol, int maxit, const bcs_options* opt,
+                     bcs_batch* out) {
+    if (!out || nsys <= 0 || !A) return BCS_ERR_ARG;
+    *out = nullptr;
     if (kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR || !(tol >= 0.0) || maxit < 0) return BCS_ERR_ARG;
-    if (nsys == 0) return BCS_OK;
     bcs_options o;
     if (opt) o = *opt; else bcs_options_default(&o);
     if (o.rr_M == 0) o.rr_M = maxit + 1;
@@ -347,140 +353,366 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
     if (rc) return rc;
     int vt_f32 = 0, valtype = 0;
     int64_t maxn = 1;
-    double sum_avg = 0.0;
     for (int k = 0; k < nsys; ++k) {
         if (!A[k] || !(A[k]->layouts & BCS_LAYOUT_CSR)) return BCS_ERR_ARG;
         if ((A[k]->n + 31) / 32 >= (int64_t)(1 << 16) * kWarps) return BCS_ERR_ARG;  // see bcs_solver_create
-        if (A[k]->n > 0 && (!b[k] || !x[k])) return BCS_ERR_ARG;
         rc = precision_types(A[k], o.precision, &vt_f32, &valtype);
         if (rc) return rc;
         maxn = std::max(maxn, A[k]->n);
-        sum_avg += A[k]->avg_row;
     }
+    // defaults measured on the 512-system cd2d batch (bcs_batch_autotune): one lane
+    // per row and clusters of two CTAs, in FP64 and FP32
     int tpr = o.threads_per_row;
-    if (!tpr) {
-        const double avg = sum_avg / nsys;
-        tpr = vt_f32 ? 8 : 1;  // FP64: one lane per row keeps shuffle-adds off the FP64 units
-        (void)avg;
-    }
+    if (!tpr) tpr = 1;
     if (tpr != 1 && tpr != 8) return BCS_ERR_ARG;
-    const int csize = o.ctas_per_sm > 0 ? o.ctas_per_sm : 4;  // CTAs per cluster
+    const int csize = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;  // CTAs per cluster
     if (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16) return BCS_ERR_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
+
+    bcs_batch bt = new (std::nothrow) bcs_batch_s();
+    if (!bt) return BCS_ERR_OOM;
+    bt->nsys = nsys;
+    bt->vt_f32 = vt_f32;
+    bt->valtype = valtype;
+    bt->tpr = tpr;
     const size_t vbytes = vt_f32 ? sizeof(float) : sizeof(double);
     // largest systems first
     std::vector<int> order(nsys);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return A[a]->nnz + A[a]->n > A[c]->nnz + A[c]->n; });
-    BatchArgs B;
+    BatchArgs& B = bt->B;
     memset(&B, 0, sizeof(B));
     B.nsys = nsys;
     B.csize = csize;
     int maxc = 0;
-    if (dispatch_b(&B, vt_f32, valtype, tpr, 0, st, &maxc) != 0 || maxc <= 0) return BCS_ERR_CUDA;
+    if (dispatch_b(&B, vt_f32, valtype, tpr, 0, nullptr, &maxc) != 0 || maxc <= 0) {
+        delete bt;
+        return BCS_ERR_CUDA;
+    }
     int nclusters = maxc;
     if (o.max_ctas > 0) nclusters = std::max(1, std::min(nclusters, o.max_ctas / csize));
     nclusters = std::min(nclusters, nsys);
+    bt->nclusters = nclusters;
     B.vec_bytes = ((size_t)maxn * vbytes + 255) / 256 * 256;
     B.ws_group_bytes = B.vec_bytes * NVEC;
-    std::vector<KParams> hp(nsys);
-    KParams* dsys = nullptr;
-    int* dorder = nullptr;
-    int* dctl = nullptr;
-    char* ws = nullptr;
-    double* parts = nullptr;
-    double* outs = nullptr;
-    std::vector<double> hout((size_t)nsys * NOUT);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float ms = 0.f;
-    int herr = 0;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (rc) return;
+        if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) rc = BCS_ERR_OOM;
+    };
+    alloc((void**)&bt->dsys, sizeof(KParams) * nsys);
+    alloc((void**)&bt->dorder, sizeof(int) * nsys);
+    alloc((void**)&bt->dctl, sizeof(int) * (2 + nclusters));  // counter, slots[nclusters], error word
+    alloc((void**)&bt->ws, B.ws_group_bytes * nclusters);
+    alloc((void**)&bt->parts, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters);
+    alloc((void**)&bt->outs, sizeof(double) * NOUT * nsys);
+    if (!rc && (cudaMallocHost((void**)&bt->hp, sizeof(KParams) * nsys) != cudaSuccess ||
+                cudaMallocHost((void**)&bt->hout, sizeof(double) * NOUT * nsys + 64) != cudaSuccess))
+        rc = BCS_ERR_OOM;
+    if (!rc && (cudaEventCreate(&bt->e0) != cudaSuccess || cudaEventCreate(&bt->e1) != cudaSuccess)) rc = BCS_ERR_CUDA;
+    if (!rc && cudaMemcpy(bt->dorder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = BCS_ERR_CUDA;
+    if (rc) {
+        bcs_batch_destroy(bt);
+        return rc;
+    }
+    bt->herr = (int*)(bt->hout + (size_t)NOUT * nsys);
+    for (int k = 0; k < nsys; ++k) {
+        KParams& P = bt->hp[k];
+        memset(&P, 0, sizeof(P));
+        bcs_matrix M = A[k];
+        bt->n.push_back(M->n);
+        P.n = M->n;
+        P.ntiles = (M->n + 31) / 32;
+        P.kind = kind;
+        P.maxit = maxit;
+        P.rr_m = o.rr_m;
+        P.rr_M = o.rr_M;
+        P.max_outer = o.max_outer;
+        P.mixed = vt_f32;
+        P.hist_cap = 0;
+        P.inner_maxit = o.inner_maxit;
+        P.inner_stall = o.inner_stall;
+        P.tol = tol;
+        P.inner_tol = o.inner_tol;
+        P.spin_budget = budget_cycles(o.spin_budget_ms);
+        P.rowptr = M->rowptr;
+        P.col = M->col;
+        P.val64 = M->val64;
+        P.val = inner_values(M, LAY_CSR, valtype);
+        P.out = bt->outs + (size_t)k * NOUT;
+        P.err = bt->dctl + 1 + nclusters;
+    }
+    B.sys = bt->dsys;
+    B.order = bt->dorder;
+    B.counter = bt->dctl;
+    B.slots = bt->dctl + 1;
+    B.ws = bt->ws;
+    B.partials = bt->parts;
+    *out = bt;
+    return BCS_OK;
+}
+
+// The launch sequence of one batched solve: parameters in, counters cleared,
+// the persistent kernel, results and the error word out.
+static int batch_enqueue(bcs_batch bt, cudaStream_t st) {
+    const int nsys = bt->nsys, nc = bt->nclusters;
+    const int csize = bt->B.csize;
+    int rc = 0;
     auto ck = [&](cudaError_t e) { if (e != cudaSuccess && !rc) rc = BCS_ERR_CUDA; };
-    ck(cudaMalloc(&dsys, sizeof(KParams) * nsys));
-    ck(cudaMalloc(&dorder, sizeof(int) * nsys));
-    ck(cudaMalloc(&dctl, sizeof(int) * (2 + nclusters)));  // counter, slots[nclusters], error word
-    if (!rc && cudaMalloc(&ws, B.ws_group_bytes * nclusters) != cudaSuccess) rc = BCS_ERR_OOM;
-    ck(cudaMalloc(&parts, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters));
-    ck(cudaMalloc(&outs, sizeof(double) * NOUT * nsys));
-    if (!rc) {
-        for (int k = 0; k < nsys; ++k) {
-            KParams& P = hp[k];
-            memset(&P, 0, sizeof(P));
-            bcs_matrix M = A[k];
-            P.n = M->n;
-            P.ntiles = (M->n + 31) / 32;
-            P.kind = kind;
-            P.maxit = maxit;
-            P.rr_m = o.rr_m;
-            P.rr_M = o.rr_M;
-            P.max_outer = o.max_outer;
-            P.mixed = vt_f32;
-            P.hist_cap = 0;
-            P.inner_maxit = o.inner_maxit;
-            P.inner_stall = o.inner_stall;
-            P.tol = tol;
-            P.inner_tol = o.inner_tol;
-            P.rowptr = M->rowptr;
-            P.col = M->col;
-            P.val64 = M->val64;
-            P.val = inner_values(M, LAY_CSR, valtype);
-            P.b = b[k];
-            P.x = x[k];
-            P.x64 = x[k];
-            P.b64 = b[k];
-            P.out = outs + (size_t)k * NOUT;
-            P.err = dctl + 1 + nclusters;
+    ck(cudaMemcpyAsync(bt->dsys, bt->hp, sizeof(KParams) * nsys, cudaMemcpyHostToDevice, st));
+    ck(cudaMemsetAsync(bt->dctl, 0, sizeof(int) * (2 + nc), st));
+    ck(cudaMemsetAsync(bt->outs, 0, sizeof(double) * NOUT * nsys, st));
+    ck(cudaMemsetAsync(bt->parts, 0, sizeof(double) * 2 * NSLOT * kRec * csize * nc, st));
+    if (!rc && dispatch_b(&bt->B, bt->vt_f32, bt->valtype, bt->tpr, nc, st, nullptr) != 0) rc = BCS_ERR_CUDA;
+    ck(cudaMemcpyAsync(bt->hout, bt->outs, sizeof(double) * NOUT * nsys, cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(bt->herr, bt->dctl + 1 + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return rc;
+}
+
+int bcs_batch_solve(bcs_batch bt, const double* const* b, double* const* x, bcs_result* res, void* stream) {
+    if (!bt || !b || !x) return BCS_ERR_ARG;
+    for (int k = 0; k < bt->nsys; ++k) {
+        if (bt->n[k] > 0 && (!b[k] || !x[k])) return BCS_ERR_ARG;
+        KParams& P = bt->hp[k];
+        P.b = b[k];
+        P.x = x[k];
+        P.x64 = x[k];
+        P.b64 = b[k];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = 0;
+    // The sequence is captured once into a CUDA graph (on a private stream) and
+    // replayed on the caller's stream: the parameter block is re-read from the
+    // same pinned host buffer at every replay.
+    if (!bt->gexec && !bt->graph_failed) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const int erc = batch_enqueue(bt, cs);
+            ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && erc == 0 && g != nullptr;
         }
-        ck(cudaMemcpyAsync(dsys, hp.data(), sizeof(KParams) * nsys, cudaMemcpyHostToDevice, st));
-        ck(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-        ck(cudaMemsetAsync(dctl, 0, sizeof(int) * (2 + nclusters), st));
-        ck(cudaMemsetAsync(outs, 0, sizeof(double) * NOUT * nsys, st));
-        ck(cudaMemsetAsync(parts, 0, sizeof(double) * 2 * NSLOT * kRec * csize * nclusters, st));
-        ck(cudaEventCreate(&e0));
-        ck(cudaEventCreate(&e1));
+        ok = ok && cudaGraphInstantiate(&bt->gexec, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (cs) cudaStreamDestroy(cs);
+        if (!ok) {
+            bt->gexec = nullptr;
+            bt->graph_failed = 1;
+            cudaGetLastError();
+        }
     }
-    if (!rc) {
-        B.sys = dsys;
-        B.order = dorder;
-        B.counter = dctl;
-        B.slots = dctl + 1;
-        B.ws = ws;
-        B.partials = parts;
-        cudaEventRecord(e0, st);
-        if (dispatch_b(&B, vt_f32, valtype, tpr, nclusters, st, nullptr) != 0) rc = BCS_ERR_CUDA;
-        cudaEventRecord(e1, st);
-        ck(cudaMemcpyAsync(hout.data(), outs, sizeof(double) * NOUT * nsys, cudaMemcpyDeviceToHost, st));
-        ck(cudaMemcpyAsync(&herr, dctl + 1 + nclusters, sizeof(int), cudaMemcpyDeviceToHost, st));
-        ck(cudaStreamSynchronize(st));
-        cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaEventRecord(bt->e0, st) != cudaSuccess) return BCS_ERR_CUDA;
+    if (bt->gexec) {
+        if (cudaGraphLaunch(bt->gexec, st) != cudaSuccess) rc = BCS_ERR_CUDA;
+    } else {
+        rc = batch_enqueue(bt, st);
     }
+    if (cudaEventRecord(bt->e1, st) != cudaSuccess && !rc) rc = BCS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = BCS_ERR_CUDA;
+    if (rc) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, bt->e0, bt->e1);
+    const int herr = *bt->herr;
     int worst = herr ? herr : BCS_OK;
-    if (!rc) {
-        for (int k = 0; k < nsys; ++k) {
-            const double* ob = hout.data() + (size_t)k * NOUT;
-            const int stt = (int)ob[O_STATUS];
-            if (stt < 0 && (worst >= 0 || stt < worst)) worst = stt;
-            else if (stt > 0 && worst == BCS_OK) worst = stt;
-            if (res) {
-                bcs_result& r = res[k];
-                memset(&r, 0, sizeof(r));
-                r.status = stt;
-                r.iterations = (int)ob[O_ITERS];
-                r.outer_steps = (int)ob[O_OUTER];
-                r.rr_steps = (int)ob[O_RR];
-                r.fallbacks = (int)ob[O_FALLBACK];
-                r.rel_res_recursive = ob[O_RECREL];
-                r.rel_res_true = ob[O_TRUEREL];
-                r.r0_norm = ob[O_R0];
-                r.seconds = ms * 1e-3;
-            }
+    for (int k = 0; k < bt->nsys; ++k) {
+        const double* ob = bt->hout + (size_t)k * NOUT;
+        const int stt = (int)ob[O_STATUS];
+        if (stt < 0 && (worst >= 0 || stt < worst)) worst = stt;
+        else if (stt > 0 && worst == BCS_OK) worst = stt;
+        if (res) {
+            bcs_result& r = res[k];
+            memset(&r, 0, sizeof(r));
+            r.status = stt;
+            r.iterations = (int)ob[O_ITERS];
+            r.outer_steps = (int)ob[O_OUTER];
+            r.rr_steps = (int)ob[O_RR];
+            r.fallbacks = (int)ob[O_FALLBACK];
+            r.rel_res_recursive = ob[O_RECREL];
+            r.rel_res_true = ob[O_TRUEREL];
+            r.r0_norm = ob[O_R0];
+            r.seconds = ms * 1e-3;
         }
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    void* ptrs[] = {dsys, dorder, dctl, ws, parts, outs};
-    for (void* p : ptrs)
+    return worst;
+}
+
+void bcs_batch_destroy(bcs_batch bt) {
+    if (!bt) return;
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->e0) cudaEventDestroy(bt->e0);
+    if (bt->e1) cudaEventDestroy(bt->e1);
+    void* dptrs[] = {bt->dsys, bt->dorder, bt->dctl, bt->ws, bt->parts, bt->outs};
+    for (void* p : dptrs)
         if (p) cudaFree(p);
-    return rc ? rc : worst;
+    if (bt->hp) cudaFreeHost(bt->hp);
+    if (bt->hout) cudaFreeHost(bt->hout);
+    delete bt;
+}
+
+int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int maxit, const bcs_options* opt,
+                      const double* const* b, double* const* x, bcs_result* res, void* stream) {
+    if (nsys < 0 || (nsys > 0 && (!A || !b || !x))) return BCS_ERR_ARG;
+    if (kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR || !(tol >= 0.0) || maxit < 0) return BCS_ERR_ARG;
+    if (nsys == 0) return BCS_OK;
+    bcs_batch bt = nullptr;
+    int rc = bcs_batch_create(nsys, A, kind, tol, maxit, opt, &bt);
+    if (rc) return rc;
+    rc = bcs_batch_solve(bt, b, x, res, stream);
+    bcs_batch_destroy(bt);
+    return rc;
+}
+
+// ---- autotuner ---------------------------------------------------------------------------
+
+namespace {
+// device vectors b = ones, x for the tuning runs
+struct TuneVecs {
+    double* b = nullptr;
+    double* x = nullptr;
+    int init(int64_t n) {
+        const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(n, 1);
+        if (cudaMalloc(&b, bytes) != cudaSuccess || cudaMalloc(&x, bytes) != cudaSuccess) return BCS_ERR_OOM;
+        std::vector<double> ones((size_t)std::max<int64_t>(n, 1), 1.0);
+        if (cudaMemcpy(b, ones.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) return BCS_ERR_CUDA;
+        return BCS_OK;
+    }
+    ~TuneVecs() {
+        if (b) cudaFree(b);
+        if (x) cudaFree(x);
+    }
+};
+// options of a timing run: fixed iteration count, no early exits
+bcs_options tune_options(const bcs_options* base, int precision) {
+    bcs_options o;
+    if (base) o = *base; else bcs_options_default(&o);
+    o.precision = precision;
+    o.max_outer = 1;
+    o.inner_tol = 1e-300;  // inner runs never stop on the tolerance
+    o.inner_stall = 0;
+    o.inner_maxit = 0;
+    o.history_len = 1;
+    return o;
+}
+}  // namespace
+
+int bcs_autotune(bcs_matrix A, int kind, int precision, int iters, bcs_tune_entry* entries, int cap, int* count,
+                 bcs_tune_entry* best, void* stream) {
+    if (!A || kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR || cap < 0 || (cap > 0 && !entries)) return BCS_ERR_ARG;
+    if (precision < BCS_FP64 || precision > BCS_BF16MAT_REFINE) return BCS_ERR_ARG;
+    int vt = 0, valtype = 0;
+    int rc = precision_types(A, precision, &vt, &valtype);
+    if (rc) return rc;
+    if (iters <= 0) iters = 20;
+    std::vector<bcs_tune_entry> cand;
+    if (A->layouts & BCS_LAYOUT_CSR)
+        for (int t : {1, 4, 8, 32}) cand.push_back({BCS_LAYOUT_CSR, t, 0, 0.0});
+    if (A->layouts & BCS_LAYOUT_SELL) cand.push_back({BCS_LAYOUT_SELL, 1, 0, 0.0});
+    TuneVecs v;
+    rc = v.init(A->n);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int bi = -1;
+    for (size_t k = 0; k < cand.size(); ++k) {
+        bcs_options o = tune_options(nullptr, precision);
+        o.layout = cand[k].layout;
+        o.threads_per_row = cand[k].layout == BCS_LAYOUT_CSR ? cand[k].threads_per_row : 0;
+        bcs_solver s = nullptr;
+        if (bcs_solver_create(A, kind, 0.0, iters, &o, &s) != BCS_OK) continue;
+        bcs_result r;
+        double t = 0.0;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            if (cudaMemsetAsync(v.x, 0, sizeof(double) * (size_t)std::max<int64_t>(A->n, 1), st) != cudaSuccess) ok = false;
+            const int e = ok ? bcs_solve(s, v.b, v.x, &r, stream) : BCS_ERR_CUDA;
+            if (e == BCS_ERR_CUDA || e == BCS_ERR_TIMEOUT || e == BCS_ERR_OOM || e == BCS_ERR_ARG) ok = false;
+            t = r.seconds / std::max(1, r.iterations);
+        }
+        bcs_solver_destroy(s);
+        if (!ok) continue;
+        cand[k].us_per_iter = t * 1e6;
+        if (bi < 0 || cand[k].us_per_iter < cand[bi].us_per_iter) bi = (int)k;
+    }
+    if (bi < 0) return BCS_ERR_CUDA;
+    A->tuned_layout[precision] = cand[bi].layout;
+    if (cand[bi].layout == BCS_LAYOUT_CSR) A->tuned_tpr[precision] = cand[bi].threads_per_row;
+    else {
+        // SELL chosen: the lanes per row of CSR-only calls (bcs_spmv) from the CSR candidates
+        int bc = -1;
+        for (size_t k = 0; k < cand.size(); ++k)
+            if (cand[k].layout == BCS_LAYOUT_CSR && cand[k].us_per_iter > 0 &&
+                (bc < 0 || cand[k].us_per_iter < cand[bc].us_per_iter))
+                bc = (int)k;
+        if (bc >= 0) A->tuned_tpr[precision] = cand[bc].threads_per_row;
+    }
+    for (int k = 0; k < cap && k < (int)cand.size(); ++k) entries[k] = cand[k];
+    if (count) *count = (int)cand.size();
+    if (best) *best = cand[bi];
+    return BCS_OK;
+}
+
+int bcs_batch_autotune(int nsys, const bcs_matrix* A, int kind, const bcs_options* opt, int iters,
+                       bcs_tune_entry* entries, int cap, int* count, bcs_options* best_opt, void* stream) {
+    if (nsys <= 0 || !A || !best_opt || cap < 0 || (cap > 0 && !entries)) return BCS_ERR_ARG;
+    if (kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR) return BCS_ERR_ARG;
+    bcs_options base;
+    if (opt) base = *opt; else bcs_options_default(&base);
+    if (iters <= 0) iters = 20;
+    int64_t tot = 0;
+    for (int k = 0; k < nsys; ++k) {
+        if (!A[k]) return BCS_ERR_ARG;
+        tot += A[k]->n;
+    }
+    // one arena for every system's b = ones and x
+    double* arena = nullptr;
+    if (cudaMalloc(&arena, sizeof(double) * 2 * (size_t)std::max<int64_t>(tot, 1)) != cudaSuccess) return BCS_ERR_OOM;
+    {
+        std::vector<double> ones((size_t)std::max<int64_t>(tot, 1), 1.0);
+        if (cudaMemcpy(arena, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(arena);
+            return BCS_ERR_CUDA;
+        }
+    }
+    std::vector<const double*> bs(nsys);
+    std::vector<double*> xs(nsys);
+    int64_t off = 0;
+    for (int k = 0; k < nsys; ++k) {
+        bs[k] = arena + off;
+        xs[k] = arena + tot + off;
+        off += A[k]->n;
+    }
+    std::vector<bcs_tune_entry> cand;
+    for (int t : {1, 8})
+        for (int c : {1, 2, 4, 8}) cand.push_back({BCS_LAYOUT_CSR, t, c, 0.0});
+    cudaStream_t st = (cudaStream_t)stream;
+    int bi = -1;
+    for (size_t k = 0; k < cand.size(); ++k) {
+        bcs_options o = tune_options(&base, base.precision);
+        o.threads_per_row = cand[k].threads_per_row;
+        o.ctas_per_sm = cand[k].cluster_ctas;
+        bcs_batch bt = nullptr;
+        if (bcs_batch_create(nsys, A, kind, 0.0, iters, &o, &bt) != BCS_OK) continue;
+        std::vector<bcs_result> res(nsys);
+        bool ok = true;
+        double t = 0.0;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            if (cudaMemsetAsync(arena + tot, 0, sizeof(double) * (size_t)std::max<int64_t>(tot, 1), st) != cudaSuccess) ok = false;
+            const int e = ok ? bcs_batch_solve(bt, bs.data(), xs.data(), res.data(), stream) : BCS_ERR_CUDA;
+            if (e == BCS_ERR_CUDA || e == BCS_ERR_TIMEOUT || e == BCS_ERR_OOM || e == BCS_ERR_ARG) ok = false;
+            t = res[0].seconds / iters;
+        }
+        bcs_batch_destroy(bt);
+        if (!ok) continue;
+        cand[k].us_per_iter = t * 1e6;
+        if (bi < 0 || cand[k].us_per_iter < cand[bi].us_per_iter) bi = (int)k;
+    }
+    cudaFree(arena);
+    if (bi < 0) return BCS_ERR_CUDA;
+    *best_opt = base;
+    best_opt->threads_per_row = cand[bi].threads_per_row;
+    best_opt->ctas_per_sm = cand[bi].cluster_ctas;
+    for (int k = 0; k < cap && k < (int)cand.size(); ++k) entries[k] = cand[k];
+    if (count) *count = (int)cand.size();
+    return BCS_OK;
 }
 
 }  // extern "C"

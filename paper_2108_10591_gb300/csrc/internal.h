@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "bcs.h"
 
 namespace bcs {
@@ -58,6 +60,21 @@ struct KParams {
     double* out;            // [NOUT]
 };
 
+// Batched solves: the systems' parameter blocks (without workspace), their
+// order, the work-list counter and each cluster's current system, and the
+// clusters' workspace (NVEC vectors of vec_bytes each) and partials.
+struct BatchArgs {
+    const KParams* sys;
+    const int* order;
+    int nsys;
+    int* counter;
+    int* slots;
+    char* ws;
+    size_t ws_group_bytes, vec_bytes;
+    double* partials;
+    int csize;
+};
+
 }  // namespace bcs
 
 struct bcs_matrix_s {
@@ -83,7 +100,8 @@ struct bcs_matrix_s {
     // row-length statistics (threads-per-row choice)
     double avg_row = 0;
     int max_row = 0;
-    int tuned_tpr = 0;
+    int tuned_tpr[3] = {0, 0, 0};     // per precision (BCS_FP64, BCS_FP32_REFINE, BCS_BF16MAT_REFINE)
+    int tuned_layout[3] = {0, 0, 0};  // BCS_LAYOUT_CSR / BCS_LAYOUT_SELL, 0 = not tuned
 };
 
 struct bcs_solver_s {
@@ -107,4 +125,24 @@ struct bcs_solver_s {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int hist_len = 0;
     int last_iters = 0;
+};
+
+// A reusable batched solve (bcs_batch_create): workspace, parameter blocks and
+// the captured launch sequence live as long as the handle.
+struct bcs_batch_s {
+    int nsys = 0, vt_f32 = 0, valtype = 0, tpr = 1, nclusters = 0;
+    std::vector<int64_t> n;
+    bcs::BatchArgs B;
+    bcs::KParams* hp = nullptr;   // pinned [nsys]
+    bcs::KParams* dsys = nullptr;
+    int* dorder = nullptr;
+    int* dctl = nullptr;
+    char* ws = nullptr;
+    double* parts = nullptr;
+    double* outs = nullptr;
+    double* hout = nullptr;       // pinned [nsys * NOUT] + error word
+    int* herr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_failed = 0;
 };

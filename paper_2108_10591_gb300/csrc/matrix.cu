@@ -220,11 +220,11 @@ int spmv_launch(bcs_matrix A, int layout, const MT* val, const VT* x, VT* y, int
 }  // namespace
 
 namespace bcs {
-// Lanes per CSR row when the caller does not choose: the autotuned value if
-// there is one, else one lane per row (no cross-lane reduction: on GB300 an
-// FP64 shuffle-add costs an FP64-pipe slot like an FMA).
-int default_tpr(const bcs_matrix_s* A) {
-    if (A->tuned_tpr) return A->tuned_tpr;
+// Lanes per CSR row when the caller does not choose: the autotuned value for
+// the precision if there is one, else one lane per row (no cross-lane
+// reduction: on GB300 an FP64 shuffle-add costs an FP64-pipe slot like an FMA).
+int default_tpr(const bcs_matrix_s* A, int precision) {
+    if (precision >= 0 && precision < 3 && A->tuned_tpr[precision]) return A->tuned_tpr[precision];
     return 1;
 }
 }  // namespace bcs
@@ -379,7 +379,9 @@ int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int ve
     if (!(A->layouts & layout)) return BCS_ERR_ARG;
     if (store != BCS_STORE_F64 && store != BCS_STORE_F32 && store != BCS_STORE_BF16) return BCS_ERR_ARG;
     if (!vec_f32 && store != BCS_STORE_F64) return BCS_ERR_ARG;  // FP64 vectors use the FP64 values
-    int tpr = threads_per_row ? threads_per_row : default_tpr(A);
+    int tpr = threads_per_row ? threads_per_row
+                              : default_tpr(A, !vec_f32 ? BCS_FP64 : store == BCS_STORE_BF16 ? BCS_BF16MAT_REFINE
+                                                                                              : BCS_FP32_REFINE);
     if (tpr != 1 && tpr != 4 && tpr != 8 && tpr != 32) return BCS_ERR_ARG;
     if (A->n == 0) return BCS_OK;
     cudaStream_t st = (cudaStream_t)stream;

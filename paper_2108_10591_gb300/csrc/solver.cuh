@@ -880,17 +880,7 @@ __device__ __forceinline__ unsigned cluster_id_x() {
 // the single-system kernel; cluster barriers replace the grid barrier.
 // sys[k]: the system's parameters without workspace; the cluster's own
 // vectors (NVEC x max_n) and partials are patched in.
-struct BatchArgs {
-    const KParams* sys;
-    const int* order;
-    int nsys;
-    int* counter;
-    int* slots;
-    char* ws;
-    size_t ws_group_bytes, vec_bytes;
-    double* partials;
-    int csize;
-};
+
 
 template <class VT, class MT, int T>
 __global__ void __launch_bounds__(kBlock) batched_kernel(const __grid_constant__ BatchArgs B) {

@@ -327,6 +327,70 @@ def test_batched(env, prec, csize):
         assert np.max(np.abs(xh - 1.0)) <= 1e-6
 
 
+def test_batch_handle_replays_with_new_vectors(env):
+    """bcs_batch: the systems fixed once, solved three times with new right-hand sides and
+    new x buffers (the first solve captures the launch sequence, the others replay it);
+    every solve is bit-identical to its own FP64 oracle solve."""
+    bcs, torch, orc = env
+    mats, _, _ = W.batch_cd2d(count=9, seed=5, kmin=8, kmax=36)
+    Ms = [bcs.csr_upload(A) for A in mats]
+    bt = bcs.Batch(Ms, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=20, ctas_per_sm=2)
+    rng = np.random.default_rng(17)
+    for rep in range(3):
+        bs_h = [orc.spmv(A, rng.uniform(0.5, 1.5, A.n)) if rep else W.rhs_ones(A) for A in mats]
+        bs = [torch.from_numpy(b).cuda() for b in bs_h]
+        xs = [torch.zeros(A.n, dtype=torch.float64, device="cuda") for A in mats]
+        code, res = bt.solve(bs, xs)
+        assert code == 0
+        for A, b, x, r in zip(mats, bs_h, xs, res):
+            ref = orc.solve(A, b, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=20, max_restarts=29)
+            assert r["status"] == 0 and r["iterations"] == ref["iterations"]
+            assert np.array_equal(x.cpu().numpy(), ref["x"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotune_records_fastest_and_solvers_use_it(env, prec):
+    """bcs_autotune times every candidate of the real solver, records the fastest for the
+    precision, and a solver created with the default (AUTO) layout and lanes per row uses
+    it: the solve converges to the FP64 tolerance (bit-identical to the oracle when the
+    chosen candidate sums each row in storage order: SELL or one lane per row)."""
+    bcs, torch, orc = env
+    A = W.cd3d_upwind(20, 50.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL, stores=bcs.STORE_F32)
+    best, cands = bcs.autotune(M, "p-BiCGSafe", precision=prec, iters=10)
+    assert len(cands) == 5 and all(c["us_per_iter"] > 0 for c in cands)
+    assert best["us_per_iter"] == min(c["us_per_iter"] for c in cands)
+    S = bcs.solver_create(M, "p-BiCGSafe", tol=1e-10, maxit=5000, precision=prec)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    r = bcs.solve(S, bd, x)
+    assert r["status"] == 0
+    xh = x.cpu().numpy()
+    assert orc.true_residual(A, b, xh) / np.linalg.norm(b) <= 1e-10
+    if prec == "fp64" and (best["layout"] == bcs.LAYOUT_SELL or best["threads_per_row"] == 1):
+        ref = orc.solve(A, b, kind="p-BiCGSafe", tol=1e-10, maxit=5000)
+        assert r["iterations"] == ref["iterations"]
+
+
+def test_batch_autotune_options_solve(env):
+    """bcs_batch_autotune measures lanes per row x cluster size on the batch and returns
+    options that bcs_batch_create accepts; the tuned batch solves every system."""
+    bcs, torch, orc = env
+    mats, _, _ = W.batch_cd2d(count=10, seed=9, kmin=8, kmax=48)
+    Ms = [bcs.csr_upload(A) for A in mats]
+    kw, cands = bcs.batch_autotune(Ms, kind="p-BiCGSafe-rr", iters=10, rr_m=20)
+    assert len(cands) == 8 and all(c["us_per_iter"] > 0 for c in cands)
+    assert kw["threads_per_row"] in (1, 8) and kw["ctas_per_sm"] in (1, 2, 4, 8)
+    bt = bcs.Batch(Ms, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, **kw)
+    bs = [torch.from_numpy(W.rhs_ones(A)).cuda() for A in mats]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    code, res = bt.solve(bs, xs)
+    assert code == 0 and all(r["status"] == 0 for r in res)
+    for A, b, x in zip(mats, bs, xs):
+        assert orc.true_residual(A, b.cpu().numpy(), x.cpu().numpy()) / np.linalg.norm(b.cpu().numpy()) <= 1e-10
+
+
 def test_barrier_timeout_is_reported_and_recoverable(env):
     """Failure detection without a GPU fault: a spin budget of a few cycles makes the
     bounded grid-barrier waits run out; the solve returns BCS_ERR_TIMEOUT (no trap, no

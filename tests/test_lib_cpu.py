@@ -47,7 +47,7 @@ def test_status_strings(bcs):
 def test_options_default(bcs):
     o = bcs.options()
     assert o.rr_m == 100 and o.precision == bcs.FP64 and o.max_outer == 30 and o.inner_tol == 1e-3
-    assert o.layout == bcs.LAYOUT_CSR and o.spin_budget_ms > 0
+    assert o.layout == bcs.LAYOUT_AUTO and o.threads_per_row == 0 and o.spin_budget_ms > 0
 
 
 def test_argument_checks_without_gpu(bcs):
