@@ -88,6 +88,8 @@ typedef struct {
     int inner_stall;      /* refinement modes: end an inner run after this many iterations without a new
                              smallest recursive residual (default 50; 0 = off); the FP64 outer step
                              then recomputes the true residual and starts a fresh Krylov space */
+    int tile_order;       /* single system: 0 = library choice, 1 = static (tile t to warp t mod warps),
+                             2 = dynamic (warps claim tiles from a counter); results do not depend on it */
 } bcs_options;
 
 typedef struct {

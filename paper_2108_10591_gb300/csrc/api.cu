@@ -14,7 +14,8 @@ using namespace bcs;
 namespace bcs {
 #define BCS_DECL(tag)                                                                                  \
     int dispatch_##tag##_0(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid); \
-    int dispatch_##tag##_1(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
+    int dispatch_##tag##_1(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid); \
+    int dispatch_##tag##_2(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
 BCS_DECL(f64)
 BCS_DECL(f32)
 BCS_DECL(bf16)
@@ -27,12 +28,20 @@ int default_tpr(const bcs_matrix_s* A, int precision);
 
 namespace {
 
-int dispatch(const KParams* P, int vt_f32, int valtype, int layout, int tpr, int grid, cudaStream_t st, int* mg) {
-    const bool sub0 = layout == LAY_SELL || tpr == 1;
-    if (!vt_f32) return sub0 ? dispatch_f64_0(P, layout, tpr, grid, st, mg) : dispatch_f64_1(P, layout, tpr, grid, st, mg);
+// dynamic tile order exists for SELL and CSR with 1 or 8 lanes per row
+bool dyn_supported(int layout, int tpr) { return layout == LAY_SELL || tpr == 1 || tpr == 8; }
+
+int dispatch(const KParams* P, int vt_f32, int valtype, int layout, int tpr, int dyn, int grid, cudaStream_t st,
+             int* mg) {
+    const int sub = (dyn && dyn_supported(layout, tpr)) ? 2 : (layout == LAY_SELL || tpr == 1) ? 0 : 1;
+    if (!vt_f32)
+        return sub == 2 ? dispatch_f64_2(P, layout, tpr, grid, st, mg)
+             : sub == 0 ? dispatch_f64_0(P, layout, tpr, grid, st, mg) : dispatch_f64_1(P, layout, tpr, grid, st, mg);
     if (valtype == VAL_F32)
-        return sub0 ? dispatch_f32_0(P, layout, tpr, grid, st, mg) : dispatch_f32_1(P, layout, tpr, grid, st, mg);
-    return sub0 ? dispatch_bf16_0(P, layout, tpr, grid, st, mg) : dispatch_bf16_1(P, layout, tpr, grid, st, mg);
+        return sub == 2 ? dispatch_f32_2(P, layout, tpr, grid, st, mg)
+             : sub == 0 ? dispatch_f32_0(P, layout, tpr, grid, st, mg) : dispatch_f32_1(P, layout, tpr, grid, st, mg);
+    return sub == 2 ? dispatch_bf16_2(P, layout, tpr, grid, st, mg)
+         : sub == 0 ? dispatch_bf16_0(P, layout, tpr, grid, st, mg) : dispatch_bf16_1(P, layout, tpr, grid, st, mg);
 }
 
 int dispatch_b(const BatchArgs* B, int vt_f32, int valtype, int tpr, int nc, cudaStream_t st, int* mc) {
@@ -81,6 +90,7 @@ int check_options(const bcs_options& o) {
     if (o.ctas_per_sm < 0 || o.ctas_per_sm > 8 || o.max_ctas < 0) return BCS_ERR_ARG;
     if (!(o.spin_budget_ms > 0.0)) return BCS_ERR_ARG;
     if (o.inner_maxit < 0 || o.inner_stall < 0) return BCS_ERR_ARG;
+    if (o.tile_order < 0 || o.tile_order > 2) return BCS_ERR_ARG;
     return BCS_OK;
 }
 
@@ -160,7 +170,11 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     const int64_t n = A->n, nn = std::max<int64_t>(n, 1);
     const int64_t ntiles = (n + 31) / 32;
     int maxg = 0;
-    if (dispatch(nullptr, s->vt_f32, s->valtype, s->layout, s->tpr, 0, 0, &maxg) != 0 || maxg <= 0) {
+    // tile order: dynamic for matrices with heavy-tailed row lengths (a warp's
+    // share of tiles then varies too much for a static split), else static
+    const bool irregular = (double)A->max_row > 4.0 * A->avg_row + 4.0;
+    s->dyn = ((o.tile_order == 2 || (o.tile_order == 0 && irregular)) && dyn_supported(s->layout, s->tpr)) ? 1 : 0;
+    if (dispatch(nullptr, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, 0, 0, &maxg) != 0 || maxg <= 0) {
         delete s;
         return BCS_ERR_CUDA;
     }
@@ -244,6 +258,7 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
     for (int v = 0; v < NVEC; ++v) P->vec[v] = (char*)s->vecmem + (size_t)v * npad * s->vbytes;
     P->partials = s->partials;
     P->bar = s->bar;
+    P->tilectr = s->dyn ? s->bar + 8 : nullptr;  // two counters, zeroed with the barrier word
     P->err = (int*)(s->bar + 4);
     P->hist = s->hist;
     P->scal = s->scal;
@@ -284,7 +299,7 @@ static int launch(bcs_solver s, const double* b, double* x, cudaStream_t st) {
     if (cudaMemsetAsync(s->bar, 0, 64, st) != cudaSuccess) return BCS_ERR_CUDA;
     if (cudaMemsetAsync(s->out, 0, sizeof(double) * NOUT, st) != cudaSuccess) return BCS_ERR_CUDA;
     cudaEventRecord(s->ev0, st);
-    const int e = dispatch(&P, s->vt_f32, s->valtype, s->layout, s->tpr, s->grid, st, nullptr);
+    const int e = dispatch(&P, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, s->grid, st, nullptr);
     cudaEventRecord(s->ev1, st);
     return e == 0 ? BCS_OK : BCS_ERR_CUDA;
 }

@@ -54,6 +54,7 @@ struct KParams {
     void* vec[NVEC];
     double* partials;       // exact partial records: [2][CTAs][NSLOT][3] 64-bit words
     unsigned* bar;          // barrier counter, zero at launch
+    unsigned* tilectr;      // two tile counters (dynamic tile order), zero at launch; nullptr: static order
     int* err;               // error flag, zero at launch
     double* hist;           // [hist_cap]
     double* scal;           // [4*hist_cap]
@@ -109,7 +110,7 @@ struct bcs_solver_s {
     int kind = 0, maxit = 0;
     double tol = 0;
     bcs_options opt;
-    int vt_f32 = 0, valtype = 0, layout = 0, tpr = 1;
+    int vt_f32 = 0, valtype = 0, layout = 0, tpr = 1, dyn = 0;
     int grid = 0;
     size_t vbytes = 0;
     void* vecmem = nullptr;       // NVEC vectors

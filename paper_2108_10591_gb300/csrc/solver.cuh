@@ -169,7 +169,7 @@ struct ClusterGroup {
     }
 };
 
-template <class VT, class MT, int LAYOUT, int T, int NW, class Group>
+template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
@@ -248,13 +248,47 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         if constexpr (kRp) return csr_tile_rp<VT, MT>(a, b, P.col, val, xv);
         else return spmv(xv, tile);
     };
-    auto stage_pro = [&](const auto& v) {
-        if (gwarp < ntiles) stg.issue(v, gwarp, 0);
-        if (gwarp + nwarps < ntiles) stg.issue(v, gwarp + nwarps, 1);
+    // Tile order of an iteration phase.  Static: tile t belongs to warp t mod
+    // nwarps.  Dynamic: the warps claim tiles from a per-phase counter (one
+    // atomic per tile, issued a tile ahead), so a warp that finishes early takes
+    // more tiles and the phase ends when the work, not the slowest warp's share,
+    // is done.  Two counters alternate between phases; entering a phase, CTA 0
+    // re-arms the other one, whose phase ended at the last grid barrier.  The
+    // inner products are exact sums, so the order of tiles changes no result.
+    constexpr bool dyn = DYN;
+    int ph = 0;
+    auto claim = [&](unsigned* c) -> int64_t {
+        unsigned v = 0u;
+        if (lane == 0) v = atomicAdd(c, 1u);
+        return (int64_t)__shfl_sync(0xffffffffu, v, 0);
     };
-    // after a tile's rows were read: refill its stage with the tile two ahead
-    auto stage_next = [&](const auto& v, int64_t tile, int64_t kt) {
-        if (tile + 2 * nwarps < ntiles) stg.issue(v, tile + 2 * nwarps, (int)(kt & 1));
+    auto tiles_begin = [&](int64_t& t0, int64_t& t1, unsigned*& c) {
+        if constexpr (dyn) {
+            c = P.tilectr + ph;
+            if (rank == 0 && threadIdx.x == 0) P.tilectr[ph ^ 1] = 0u;
+            ph ^= 1;
+            t0 = claim(c);
+            t1 = claim(c);
+        } else {
+            c = nullptr;
+            t0 = gwarp;
+            t1 = gwarp + nwarps;
+        }
+    };
+    // the tile after t1 (static: t1 + nwarps)
+    auto tiles_next = [&](int64_t t1, unsigned* c) -> int64_t {
+        if constexpr (dyn) return claim(c);
+        else return t1 + nwarps;
+    };
+    // stage the warp's first two tiles of a phase (after the grid barrier that
+    // made the previous phase's writes visible)
+    auto stage_two = [&](const auto& v, int64_t t0, int64_t t1) {
+        if (t0 < ntiles) stg.issue(v, t0, 0);
+        if (t1 < ntiles) stg.issue(v, t1, 1);
+    };
+    // after a tile's rows were read: refill its stage with tile t (two ahead)
+    auto stage_at = [&](const auto& v, int64_t t, int64_t kt) {
+        if (t < ntiles) stg.issue(v, t, (int)(kt & 1));
     };
 
     // ---- SELL: the solve runs in the permuted row order ----
@@ -365,16 +399,23 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
             typename DotAccOf<VT>::type xv[10];
             VT as_first = VT(0);
+            int64_t pa0 = 0, pa1 = 0;   // p-BiCGSafe phase A: the warp's first two tiles
+            unsigned* pac = nullptr;
             if (kind == BCS_SSBICGSAFE2) {
                 // phase A: s_i = A r_i and the products involving s_i
                 wa_init10(xv);
                 const VT* const vPA[] = {Y, R, RS};
-                stage_pro(vPA);
+                int64_t t0, t1;
+                unsigned* tc;
+                tiles_begin(t0, t1, tc);
+                stage_two(vPA, t0, t1);
                 int rpa = 0, rpb = 0;
-                if (kRp) rp_load(gwarp, rpa, rpb);
-                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
+                if (kRp) rp_load(t0, rpa, rpb);
+                for (int64_t kt = 0; t0 < ntiles; ++kt) {
+                    const int64_t tile = t0;
+                    const int64_t t2 = tiles_next(t1, tc);
                     int rpa_n = 0, rpb_n = 0;
-                    if (kRp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    if (kRp) rp_load(t1, rpa_n, rpb_n);
                     const VT sv = spmv_rp(R, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
@@ -399,7 +440,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
-                    stage_next(vPA, tile, kt);
+                    stage_at(vPA, t2, kt);
+                    t0 = t1;
+                    t1 = t2;
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(cur));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
@@ -408,8 +451,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // iteration i are reduced (the overlap of the reduction with MV, Section 3)
                 if (!rr_step) {
                     const VT* const vA0[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
-                    stage_pro(vA0);
-                    if (gwarp < ntiles) as_first = spmv(sCur, gwarp);
+                    tiles_begin(pa0, pa1, pac);
+                    stage_two(vA0, pa0, pa1);
+                    if (pa0 < ntiles) as_first = spmv(sCur, pa0);
                 }
             }
             reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
@@ -509,8 +553,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             if (kind == BCS_SSBICGSAFE2) {
                 // phase B: p_i, o_i, u_i
                 const VT* const vPB[] = {R, sCur, Tv, Y, Pv, U};
-                stage_pro(vPB);
-                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
+                int64_t b0, b1;
+                unsigned* tb;
+                tiles_begin(b0, b1, tb);
+                stage_two(vPB, b0, b1);
+                for (int64_t kt = 0; b0 < ntiles; ++kt) {
+                    const int64_t tile = b0;
+                    const int64_t b2 = tiles_next(b1, tb);
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     if (row < n) {
@@ -521,18 +570,25 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         u = vfma(ze, o, et * vfma(be, u, y));
                         Pv[row] = p; O[row] = o; U[row] = u;
                     }
-                    stage_next(vPB, tile, kt);
+                    stage_at(vPB, b2, kt);
+                    b0 = b1;
+                    b1 = b2;
                 }
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
                 wa_init10(xv);
                 const VT* const vPC[] = {O, R, U, sCur, Y, Pv, RS, Z};
-                stage_pro(vPC);
+                int64_t c0, c1;
+                unsigned* tcc;
+                tiles_begin(c0, c1, tcc);
+                stage_two(vPC, c0, c1);
                 int rpa = 0, rpb = 0;
-                if (kRp) rp_load(gwarp, rpa, rpb);
-                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
+                if (kRp) rp_load(c0, rpa, rpb);
+                for (int64_t kt = 0; c0 < ntiles; ++kt) {
+                    const int64_t tile = c0;
+                    const int64_t c2 = tiles_next(c1, tcc);
                     int rpa_n = 0, rpb_n = 0;
-                    if (kRp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    if (kRp) rp_load(c1, rpa_n, rpb_n);
                     const VT w = spmv_rp(U, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
@@ -568,7 +624,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
-                    stage_next(vPC, tile, kt);
+                    stage_at(vPC, c2, kt);
+                    c0 = c1;
+                    c1 = c2;
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
@@ -577,12 +635,14 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_init10(xv);
                 const VT* const vA[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
                 int rpa = 0, rpb = 0;
-                if (kRp) rp_load(gwarp + nwarps, rpa, rpb);
-                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
+                if (kRp) rp_load(pa1, rpa, rpb);
+                for (int64_t kt = 0; pa0 < ntiles; ++kt) {
+                    const int64_t tile = pa0;
+                    const int64_t pa2 = tiles_next(pa1, pac);
                     int rpa_n = 0, rpb_n = 0;
-                    if (kRp && tile > gwarp) rp_load(tile + nwarps, rpa_n, rpb_n);
-                    const VT As = (tile == gwarp) ? as_first : spmv_rp(sCur, tile, rpa, rpb);
-                    if (tile > gwarp) { rpa = rpa_n; rpb = rpb_n; }
+                    if (kRp && kt > 0) rp_load(pa1, rpa_n, rpb_n);
+                    const VT As = (kt == 0) ? as_first : spmv_rp(sCur, tile, rpa, rpb);
+                    if (kt > 0) { rpa = rpa_n; rpb = rpb_n; }
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
@@ -625,19 +685,26 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
-                    stage_next(vA, tile, kt);
+                    stage_at(vA, pa2, kt);
+                    pa0 = pa1;
+                    pa1 = pa2;
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
                 wa_init10(xv);
                 const VT* const vC[] = {L, G, sNxt, Y, R, RS};
-                stage_pro(vC);
+                int64_t c0, c1;
+                unsigned* tcc;
+                tiles_begin(c0, c1, tcc);
+                stage_two(vC, c0, c1);
                 rpa = 0; rpb = 0;
-                if (kRp) rp_load(gwarp, rpa, rpb);
-                for (int64_t tile = gwarp, kt = 0; tile < ntiles; tile += nwarps, ++kt) {
+                if (kRp) rp_load(c0, rpa, rpb);
+                for (int64_t kt = 0; c0 < ntiles; ++kt) {
+                    const int64_t tile = c0;
+                    const int64_t c2 = tiles_next(c1, tcc);
                     int rpa_n = 0, rpb_n = 0;
-                    if (kRp) rp_load(tile + nwarps, rpa_n, rpb_n);
+                    if (kRp) rp_load(c1, rpa_n, rpb_n);
                     const VT Aw = spmv_rp(W, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
@@ -666,7 +733,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
-                    stage_next(vC, tile, kt);
+                    stage_at(vC, c2, kt);
+                    c0 = c1;
+                    c1 = c2;
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
@@ -797,10 +866,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     }
 }
 
-template <class VT, class MT, int LAYOUT, int T>
+template <class VT, class MT, int LAYOUT, int T, bool DYN>
 __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
-    solve_body<VT, MT, LAYOUT, T, kSolveWarps>(P, grp);
+    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN>(P, grp);
 }
 
 // dynamic shared memory of the solver kernels: the per-warp staging buffers and their mbarriers
@@ -809,48 +878,54 @@ constexpr size_t stage_smem_bytes() {
     return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT) + (size_t)NW * 2 * sizeof(unsigned long long);
 }
 
-template <class VT, class MT, int LAYOUT, int T>
+template <class VT, class MT, int LAYOUT, int T, bool DYN>
 int launch_one(const KParams& P, int grid, cudaStream_t st) {
     void* args[] = {(void*)&P};
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
-    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T>,
+    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T>, dim3(grid), dim3(kSolveBlock),
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN>, dim3(grid), dim3(kSolveBlock),
                                             args, smem, st);
 }
 
-template <class VT, class MT, int LAYOUT, int T>
+template <class VT, class MT, int LAYOUT, int T, bool DYN>
 int max_grid_one(int* grid) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T>,
+        e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T>, kSolveBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T, DYN>, kSolveBlock, smem);
     *grid = sms * per;
     return (int)e;
 }
 
 // Dispatch over layout and lanes-per-row for one (VT, MT) pair; each
 // translation unit instantiates one subset (SUBSET 0: SELL and CSR with 1 lane
-// per row, SUBSET 1: CSR with 4, 8 or 32 lanes per row).
+// per row, SUBSET 1: CSR with 4, 8 or 32 lanes per row, both in the static
+// tile order; SUBSET 2: the dynamic tile order for SELL and CSR with 1 or 8
+// lanes per row).
 template <class VT, class MT, int SUBSET>
 int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
-#define BCS_CASE(LAY, TT)                                                              \
-    return P ? launch_one<VT, MT, LAY, TT>(*P, grid, st) : max_grid_one<VT, MT, LAY, TT>(max_grid)
+#define BCS_CASE(LAY, TT, D)                                                              \
+    return P ? launch_one<VT, MT, LAY, TT, D>(*P, grid, st) : max_grid_one<VT, MT, LAY, TT, D>(max_grid)
     if constexpr (SUBSET == 0) {
-        if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1); }
-        BCS_CASE(LAY_CSR, 1);
-    } else {
+        if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1, false); }
+        BCS_CASE(LAY_CSR, 1, false);
+    } else if constexpr (SUBSET == 1) {
         switch (tpr) {
-            case 4: BCS_CASE(LAY_CSR, 4);
-            case 8: BCS_CASE(LAY_CSR, 8);
-            default: BCS_CASE(LAY_CSR, 32);
+            case 4: BCS_CASE(LAY_CSR, 4, false);
+            case 8: BCS_CASE(LAY_CSR, 8, false);
+            default: BCS_CASE(LAY_CSR, 32, false);
         }
+    } else {
+        if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1, true); }
+        if (tpr == 8) { BCS_CASE(LAY_CSR, 8, true); }
+        BCS_CASE(LAY_CSR, 1, true);
     }
 #undef BCS_CASE
 }
@@ -901,7 +976,7 @@ __global__ void __launch_bounds__(kBlock) batched_kernel(const __grid_constant__
             sP.partials = B.partials + (size_t)cid * 2 * B.csize * NSLOT * kRec;
         }
         __syncthreads();
-        solve_body<VT, MT, LAY_CSR, T, kWarps>(sP, grp);
+        solve_body<VT, MT, LAY_CSR, T, kWarps, false>(sP, grp);
     }
 }
 

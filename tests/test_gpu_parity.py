@@ -391,6 +391,23 @@ def test_batch_autotune_options_solve(env):
         assert orc.true_residual(A, b.cpu().numpy(), x.cpu().numpy()) / np.linalg.norm(b.cpu().numpy()) <= 1e-10
 
 
+@pytest.mark.parametrize("cfg", [dict(threads_per_row=1), dict(layout="sell")])
+def test_dynamic_tile_order_bit_identical(env, cfg):
+    """Warps claiming tiles from a counter (the order used for irregular matrices) change
+    which lane sums which rows, but the inner products are exact sums: the FP64 solve is
+    bit-identical to the static order and to the oracle (power-law rows up to 512)."""
+    bcs, torch, orc = env
+    A = W.powerlaw(n=30000, seed=4)
+    b = W.rhs_ones(A)
+    rs, xs_, hs, ss = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe-rr", tile_order=1, **cfg)
+    rd, xd_, hd, sd = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe-rr", tile_order=2, **cfg)
+    ref = orc.solve(A, b, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=100, max_restarts=29)
+    assert rs["status"] == rd["status"] == 0
+    assert rs["iterations"] == rd["iterations"] == ref["iterations"]
+    assert np.array_equal(xs_, xd_) and np.array_equal(xd_, ref["x"])
+    assert np.array_equal(hs, hd) and np.array_equal(ss, sd)
+
+
 def test_barrier_timeout_is_reported_and_recoverable(env):
     """Failure detection without a GPU fault: a spin budget of a few cycles makes the
     bounded grid-barrier waits run out; the solve returns BCS_ERR_TIMEOUT (no trap, no
