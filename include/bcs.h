@@ -73,7 +73,7 @@ typedef struct {
     int rr_m;             /* Alg. 5 replacement epoch m (default 100; Section 5.2 uses 100 and 96) */
     int rr_M;             /* Alg. 5 replacement limit M: replace only while i < M (default: maxit) */
     int precision;        /* BCS_FP64 (default) | BCS_FP32_REFINE | BCS_BF16MAT_REFINE */
-    double inner_tol;     /* refinement modes: inner stop at ||r_inner|| <= inner_tol*||r_outer|| (default 1e-3) */
+    double inner_tol;     /* refinement modes: inner stop at ||r_inner|| <= inner_tol*||r_outer|| (default 1e-2) */
     int max_outer;        /* outer steps: true-residual checks / restarts / refinement steps (default 30) */
     int history_len;      /* capacity of the residual history (default 4096 entries) */
     int layout;           /* BCS_LAYOUT_AUTO (default: tuned, else CSR), BCS_LAYOUT_CSR or BCS_LAYOUT_SELL
@@ -86,7 +86,7 @@ typedef struct {
     double spin_budget_ms;/* per grid-barrier wait before BCS_ERR_TIMEOUT (default 2000 ms) */
     int inner_maxit;      /* refinement modes: at most this many iterations per inner run (0 = no cap) */
     int inner_stall;      /* refinement modes: end an inner run after this many iterations without a new
-                             smallest recursive residual (default 50; 0 = off); the FP64 outer step
+                             smallest recursive residual (default 20; 0 = off); the FP64 outer step
                              then recomputes the true residual and starts a fresh Krylov space */
     int tile_order;       /* single system: 0 = library choice, 1 = static (tile t to warp t mod warps),
                              2 = dynamic (warps claim tiles from a counter); results do not depend on it */

@@ -104,7 +104,7 @@ void bcs_options_default(bcs_options* o) {
     o->rr_m = 100;
     o->rr_M = 0;  // 0 = maxit
     o->precision = BCS_FP64;
-    o->inner_tol = 1e-3;
+    o->inner_tol = 1e-2;
     o->max_outer = 30;
     o->history_len = 4096;
     o->layout = BCS_LAYOUT_AUTO;
@@ -113,7 +113,7 @@ void bcs_options_default(bcs_options* o) {
     o->max_ctas = 0;
     o->spin_budget_ms = 2000.0;
     o->inner_maxit = 0;
-    o->inner_stall = 50;
+    o->inner_stall = 20;
 }
 
 const char* bcs_status_string(int s) {

@@ -46,7 +46,7 @@ def test_status_strings(bcs):
 
 def test_options_default(bcs):
     o = bcs.options()
-    assert o.rr_m == 100 and o.precision == bcs.FP64 and o.max_outer == 30 and o.inner_tol == 1e-3
+    assert o.rr_m == 100 and o.precision == bcs.FP64 and o.max_outer == 30 and o.inner_tol == 1e-2 and o.inner_stall == 20
     assert o.layout == bcs.LAYOUT_AUTO and o.threads_per_row == 0 and o.spin_budget_ms > 0
 
 
