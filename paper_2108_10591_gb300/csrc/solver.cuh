@@ -108,47 +108,68 @@ __device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage<NW>& st, uns
 
 // Sum every CTA's record exactly (all CTAs obtain the same values) and round
 // each slot once: out[k] = correctly rounded slot k, for the first NS slots.
-// G = NW / NS warps share a slot; each lane loads its records in batches of
-// four (one memory round trip for up to 128 G records), merges them, and the
-// warp, then the slot's G warps, add their aligned partials.
+// One warp per slot: its lanes take the records c = lane, lane + 32, ...; the
+// slot's common anchor is the largest record anchor, every record is shifted
+// to it and the lanes add plain 192-bit integers (records are below 2^136,
+// so 2^17 of them cannot overflow), then a warp sum and one rounding.
+// reduce_issue pulls the slot's records into L1 ahead of reduce_finish, so
+// that the caller can overlap that memory round trip with other work.
 template <int NS, int NW>
-__device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage<NW>& st, double* out) {
+__device__ __forceinline__ void reduce_issue(const unsigned long long* base, int nblk) {
     static_assert(NS >= 1 && NS <= 10, "slots");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int G = NW >= NS ? NW / NS : 1;
-    constexpr int PASSES = NW >= NS ? 1 : (NS + NW - 1) / NW;
-    constexpr int kBatch = 4;
+    for (int k = warp; k < NS; k += NW)
+        for (int c = lane; c < nblk; c += 32)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(base + k * kRec + (size_t)c * NSLOT * kRec));
+}
+
+template <int NS, int NW>
+__device__ __forceinline__ void reduce_finish(const unsigned long long* base, int nblk, XStage<NW>& st, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    (void)st;
 #pragma unroll 1
-    for (int pass = 0; pass < PASSES; ++pass) {
-        const int k = NW >= NS ? warp / G : warp + pass * NW;
-        const int g = NW >= NS ? warp % G : 0;
-        if (k < NS) {
-            XAcc a;
-            xa_init(a);
-            const unsigned long long* rk = base + k * kRec;
-            for (int c0 = g * 32 + lane; c0 < nblk; c0 += kBatch * G * 32) {
-                XAcc t[kBatch];
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int c = c0 + u * G * 32;
-                    if (c < nblk) t[u] = load_rec(rk + (size_t)c * NSLOT * kRec);
-                    else xa_init(t[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) xa_merge(a, t[u]);
-            }
-            a = xa_warp_aligned_sum(a);
-            if (lane == 0) st.w[k][g] = a;
-        }
-    }
-    __syncthreads();
     for (int k = warp; k < NS; k += NW) {
-        XAcc t;
-        if (lane < G) t = st.w[k][lane]; else xa_init(t);
-        t = xa_warp_aligned_sum(t);
-        if (lane == 0) out[k] = xa_round(t);
+        const unsigned long long* rk = base + k * kRec;
+        int E = kXaEmpty;
+        for (int c = lane; c < nblk; c += 32) {
+            const int e = (int)(long long)rk[(size_t)c * NSLOT * kRec];
+            E = e > E ? e : E;
+        }
+        E = warp_max_int(E);
+        double res;
+        if (E == kXaNaN) {
+            res = __longlong_as_double(0x7FF8000000000000ll);
+        } else if (E == kXaEmpty) {
+            res = 0.0;
+        } else {
+            XAcc a;
+            a.e = E;
+            a.w2 = a.w1 = a.w0 = 0ull;
+            for (int c = lane; c < nblk; c += 32) {
+                XAcc t = load_rec(rk + (size_t)c * NSLOT * kRec);
+                if (t.e == kXaEmpty) continue;
+                xa_sar192(t, E - t.e);
+                xa_add192(a, t.w2, t.w1, t.w0);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long b0 = __shfl_xor_sync(0xffffffffu, a.w0, off);
+                const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, a.w1, off);
+                const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, a.w2, off);
+                xa_add192(a, b2, b1, b0);
+            }
+            xa_norm(a);
+            res = xa_round(a);
+        }
+        if (lane == 0) out[k] = res;
     }
     __syncthreads();
+}
+
+template <int NS, int NW>
+__device__ __forceinline__ void reduce_partials(const unsigned long long* base, int nblk, XStage<NW>& st, double* out) {
+    reduce_issue<NS, NW>(base, nblk);
+    reduce_finish<NS, NW>(base, nblk, st, out);
 }
 
 // A set of CTAs that solve one system together: the whole cooperative grid
@@ -450,13 +471,17 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase A: A s_i of the first tile is in flight while the partials of
                 // iteration i are reduced (the overlap of the reduction with MV, Section 3)
                 if (!rr_step) {
+                    reduce_issue<9, NW>(rbase(cur), nblk);   // records travel to L1 during the SpMV
                     const VT* const vA0[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
                     tiles_begin(pa0, pa1, pac);
                     stage_two(vA0, pa0, pa1);
                     if (pa0 < ntiles) as_first = spmv(sCur, pa0);
+                    reduce_finish<9, NW>(rbase(cur), nblk, s_x, s_sum);
+                } else {
+                    reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
                 }
             }
-            reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
+            if (kind == BCS_SSBICGSAFE2) reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
 
             // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
             // The independent quotients are formed side by side by the lanes of
