@@ -40,9 +40,9 @@ SM_MAX_MHZ = 2070.0
 # workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
 # iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
 # for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
-TRAFFIC = {"fp64": {"per_iter": 929.4e6, "per_outer": 1013.2e6},
-           "fp32": {"per_iter": 525.0e6, "per_outer": 822.8e6}}
-KERNEL_SHA = "be25a675e106046f"
+TRAFFIC = {"fp64": {"per_iter": 931.1e6, "per_outer": 1014.1e6},
+           "fp32": {"per_iter": 525.1e6, "per_outer": 824.2e6}}
+KERNEL_SHA = "c0255c26f6814855"
 
 
 def kernel_sources_sha():
@@ -434,7 +434,7 @@ def main():
     if (tr and a.kind == "p-BiCGSafe" and a.layout == "csr" and a.size == 128 and a.tpr in (0, 1)
             and kernel_sources_sha() == KERNEL_SHA):
         traffic = tr["per_iter"] * iters + tr["per_outer"] * outer
-    kname = "solve_kernel<%s,%s,%s>" % ("float" if lo else "double",
+    kname = "solve_kernel<%s,%s,%s,1,static>" % ("float" if lo else "double",
                                         {"fp64": "double", "fp32": "float", "bf16": "bf16"}[a.precision],
                                         a.layout.upper())
     hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
