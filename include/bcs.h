@@ -102,6 +102,11 @@ typedef struct {
     double rel_res_true;      /* ||b - A x||_2 / ||b - A x_0||_2 in FP64 at exit */
     double r0_norm;           /* ||b - A x_0||_2 */
     double seconds;           /* device time of the solve (CUDA events) */
+    int grid_syncs;           /* grid-wide (or cluster) barriers the solve passed */
+    int reductions;           /* grid-wide reductions of inner-product partials (one per iteration,
+                                 plus one per true-residual check) */
+    int spmv_passes;          /* passes over the matrix (two per iteration, Table 1; plus set-up,
+                                 true-residual checks and five per residual replacement) */
 } bcs_result;
 
 /* Fill *opt with the defaults listed above. */

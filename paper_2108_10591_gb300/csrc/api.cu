@@ -287,6 +287,9 @@ static int finish(bcs_solver s, cudaStream_t st, bcs_result* res) {
         res->rel_res_recursive = o[O_RECREL];
         res->rel_res_true = o[O_TRUEREL];
         res->r0_norm = o[O_R0];
+        res->grid_syncs = (int)o[O_SYNCS];
+        res->reductions = (int)o[O_REDUCTIONS];
+        res->spmv_passes = (int)o[O_SPMV];
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, s->ev0, s->ev1) == cudaSuccess) res->seconds = ms * 1e-3;
     }
@@ -305,6 +308,7 @@ static int launch(bcs_solver s, const double* b, double* x, cudaStream_t st) {
 }
 
 int bcs_solve(bcs_solver s, const double* b_dev, double* x_dev, bcs_result* res, void* stream) {
+    NvtxRange nv("bcs_solve");
     if (!s || (s->A->n > 0 && (!b_dev || !x_dev))) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (s->A->n == 0) {
@@ -317,6 +321,7 @@ int bcs_solve(bcs_solver s, const double* b_dev, double* x_dev, bcs_result* res,
 }
 
 int bcs_solve_host(bcs_solver s, const double* b_host, double* x_host, bcs_result* res, void* stream) {
+    NvtxRange nv("bcs_solve_host");
     if (!s || (s->A->n > 0 && (!b_host || !x_host))) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = s->A->n;
@@ -484,6 +489,7 @@ static int batch_enqueue(bcs_batch bt, cudaStream_t st) {
 }
 
 int bcs_batch_solve(bcs_batch bt, const double* const* b, double* const* x, bcs_result* res, void* stream) {
+    NvtxRange nv("bcs_batch_solve");
     if (!bt || !b || !x) return BCS_ERR_ARG;
     for (int k = 0; k < bt->nsys; ++k) {
         if (bt->n[k] > 0 && (!b[k] || !x[k])) return BCS_ERR_ARG;
@@ -545,6 +551,9 @@ int bcs_batch_solve(bcs_batch bt, const double* const* b, double* const* x, bcs_
             r.rel_res_recursive = ob[O_RECREL];
             r.rel_res_true = ob[O_TRUEREL];
             r.r0_norm = ob[O_R0];
+            r.grid_syncs = (int)ob[O_SYNCS];
+            r.reductions = (int)ob[O_REDUCTIONS];
+            r.spmv_passes = (int)ob[O_SPMV];
             r.seconds = ms * 1e-3;
         }
     }
@@ -612,6 +621,7 @@ bcs_options tune_options(const bcs_options* base, int precision) {
 
 int bcs_autotune(bcs_matrix A, int kind, int precision, int iters, bcs_tune_entry* entries, int cap, int* count,
                  bcs_tune_entry* best, void* stream) {
+    NvtxRange nv("bcs_autotune");
     if (!A || kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR || cap < 0 || (cap > 0 && !entries)) return BCS_ERR_ARG;
     if (precision < BCS_FP64 || precision > BCS_BF16MAT_REFINE) return BCS_ERR_ARG;
     int vt = 0, valtype = 0;
@@ -667,6 +677,7 @@ int bcs_autotune(bcs_matrix A, int kind, int precision, int iters, bcs_tune_entr
 
 int bcs_batch_autotune(int nsys, const bcs_matrix* A, int kind, const bcs_options* opt, int iters,
                        bcs_tune_entry* entries, int cap, int* count, bcs_options* best_opt, void* stream) {
+    NvtxRange nv("bcs_batch_autotune");
     if (nsys <= 0 || !A || !best_opt || cap < 0 || (cap > 0 && !entries)) return BCS_ERR_ARG;
     if (kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR) return BCS_ERR_ARG;
     bcs_options base;

@@ -5,9 +5,20 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bcs.h"
 
 namespace bcs {
+
+// Named range on the profiler timeline (NVTX) for the duration of a scope;
+// costs a branch when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Slots of the per-CTA inner-product partials (Alg. 3/4: a..h and r; plus the
 // FP64 true-residual norm of the outer step).
@@ -18,7 +29,8 @@ enum Slot { SA = 0, SB, SC, SD, SE, SF, SG, SH, SR, ST, NSLOT_USED, NSLOT = 16 }
 enum Vec { V_R = 0, V_RS, V_S, V_S2, V_Y, V_T, V_P, V_U, V_Z, V_W, V_L, V_G, V_O, V_BIN, V_D, NVEC };
 
 // Result block written by CTA 0 at the end of a solve (device memory).
-enum Out { O_STATUS = 0, O_ITERS, O_OUTER, O_RR, O_FALLBACK, O_RECREL, O_TRUEREL, O_R0, O_HISTLEN, NOUT = 16 };
+enum Out { O_STATUS = 0, O_ITERS, O_OUTER, O_RR, O_FALLBACK, O_RECREL, O_TRUEREL, O_R0, O_HISTLEN, O_SYNCS, O_REDUCTIONS,
+           O_SPMV, NOUT = 16 };
 
 enum Layout { LAY_CSR = 0, LAY_SELL = 1 };
 enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };

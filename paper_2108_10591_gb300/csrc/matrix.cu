@@ -233,6 +233,7 @@ extern "C" {
 
 int bcs_csr_upload(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
                    int layouts, int sell_C, int sell_sigma, int stores, void* stream, bcs_matrix* out) {
+    NvtxRange nv("bcs_csr_upload");
     if (!out) return BCS_ERR_ARG;
     *out = nullptr;
     if (n < 0 || nnz < 0 || n >= (1ll << 31) || nnz >= (1ll << 31)) return BCS_ERR_ARG;

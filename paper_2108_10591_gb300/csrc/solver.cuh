@@ -177,14 +177,20 @@ __device__ __forceinline__ void reduce_partials(const unsigned long long* base, 
 struct GridGroup {
     GridBarrier gb;
     int rank, size;
-    __device__ bool sync(volatile int* flag) { return gb.sync(flag); }
+    int nsync = 0;   // grid barriers passed (reported with the result)
+    __device__ bool sync(volatile int* flag) {
+        ++nsync;
+        return gb.sync(flag);
+    }
 };
 struct ClusterGroup {
     int rank, size;
+    int nsync = 0;
     // barrier.cluster with release/acquire semantics: every write of the
     // cluster's threads before the barrier is visible after it.  All CTAs of
     // a cluster are co-scheduled, so the wait always ends.
     __device__ bool sync(volatile int*) {
+        ++nsync;
         asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
         return true;
     }
@@ -326,6 +332,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     }
 
     int status = BCS_NOT_CONVERGED, inner_status = BCS_OK;
+    int n_spmv = 0, n_red = 0;  // passes over the matrix and grid reductions (reported with the result)
+    grp.nsync = 0;
     int total = 0, evals = 0, runs = 0, hist_len = 0, rr_steps = 0, fallbacks = 0;
     double r0n = 0.0, thresh = 0.0, r0ref = 1.0, rtrue = 0.0, last_rec = 0.0;
     double alpha_p = 0.0, zeta_p = 0.0, f_p = 0.0;  // thread 0 of each CTA
@@ -369,6 +377,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             flush_partials<(1u << ST)>(xt, s_x, myrec(0));
             if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
             reduce_partials<10>(rbase(0), nblk, s_x, s_sum);
+            ++n_spmv;
+            ++n_red;
             const double rt2 = s_sum[ST];
             rtrue = sqrt(rt2);
             if (evals == 0) {
@@ -389,6 +399,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         if (kind != BCS_SSBICGSAFE2) {
             typename DotAccOf<VT>::type xv[10];
             wa_init10(xv);
+            ++n_spmv;
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const VT sv = spmv(R, tile);
                 const int64_t row = tile * 32 + lane;
@@ -426,6 +437,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase A: s_i = A r_i and the products involving s_i
                 wa_init10(xv);
                 const VT* const vPA[] = {Y, R, RS};
+                ++n_spmv;
                 int64_t t0, t1;
                 unsigned* tc;
                 tiles_begin(t0, t1, tc);
@@ -482,6 +494,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
             }
             if (kind == BCS_SSBICGSAFE2) reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
+            ++n_red;
 
             // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
             // The independent quotients are formed side by side by the lanes of
@@ -603,6 +616,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
                 wa_init10(xv);
                 const VT* const vPC[] = {O, R, U, sCur, Y, Pv, RS, Z};
+                ++n_spmv;
                 int64_t c0, c1;
                 unsigned* tcc;
                 tiles_begin(c0, c1, tcc);
@@ -657,6 +671,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
             } else if (!rr_step) {
                 // phase A (continued): fused recurrences of Alg. 4
+                ++n_spmv;  // A s_i (its first tile already above)
                 wa_init10(xv);
                 const VT* const vA[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
                 int rpa = 0, rpb = 0;
@@ -719,6 +734,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
                 wa_init10(xv);
                 const VT* const vC[] = {L, G, sNxt, Y, R, RS};
+                ++n_spmv;
                 int64_t c0, c1;
                 unsigned* tcc;
                 tiles_begin(c0, c1, tcc);
@@ -858,6 +874,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
                 ++rr_steps;
+                n_spmv += 5;  // w = A u; A x, A t, A y; s = A r
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
             }
         }
@@ -882,6 +899,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         P.out[O_TRUEREL] = rtrue / r0ref;
         P.out[O_R0] = r0n;
         P.out[O_HISTLEN] = hist_len;
+        P.out[O_SYNCS] = grp.nsync;
+        P.out[O_REDUCTIONS] = n_red;
+        P.out[O_SPMV] = n_spmv;
     }
     if (P.perm != nullptr) {
         for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {

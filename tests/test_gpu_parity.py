@@ -408,6 +408,35 @@ def test_dynamic_tile_order_bit_identical(env, cfg):
     assert np.array_equal(hs, hd) and np.array_equal(ss, sd)
 
 
+def test_table1_operation_counts(env):
+    """Table 1: one iteration of either method costs two passes over the matrix and one
+    grid-wide reduction of the inner products; p-BiCGSafe needs two grid barriers per
+    iteration (the reduction overlapped with A s_i), ssBiCGSafe2 three; a residual
+    replacement step of Alg. 5 costs five passes and four barriers.  Counted on the device
+    and compared between runs of k and k + 1 iterations."""
+    bcs, torch, orc = env
+    A = W.cd2d(40, 10.0)
+    b = W.rhs_ones(A)
+
+    def run(kind, k, **kw):
+        r = _gpu_solve(bcs, torch, A, b, kind, tol=0.0, maxit=k, max_outer=1, **kw)[0]
+        assert r["iterations"] == k
+        return r
+
+    for kind, syncs in [("p-BiCGSafe", 2), ("ssBiCGSafe2", 3)]:
+        for prec in ["fp64", "fp32"]:
+            r0, r1 = run(kind, 10, precision=prec), run(kind, 11, precision=prec)
+            assert r1["spmv_passes"] - r0["spmv_passes"] == 2
+            assert r1["reductions"] - r0["reductions"] == 1
+            assert r1["grid_syncs"] - r0["grid_syncs"] == syncs
+    # p-BiCGSafe-rr with m = 4: the update at i = 4 is a replacement step
+    r0, r1 = run("p-BiCGSafe-rr", 4, rr_m=4), run("p-BiCGSafe-rr", 5, rr_m=4)
+    assert (r1["rr_steps"], r0["rr_steps"]) == (1, 0)
+    assert r1["spmv_passes"] - r0["spmv_passes"] == 5
+    assert r1["reductions"] - r0["reductions"] == 1
+    assert r1["grid_syncs"] - r0["grid_syncs"] == 4
+
+
 def test_barrier_timeout_is_reported_and_recoverable(env):
     """Failure detection without a GPU fault: a spin budget of a few cycles makes the
     bounded grid-barrier waits run out; the solve returns BCS_ERR_TIMEOUT (no trap, no
