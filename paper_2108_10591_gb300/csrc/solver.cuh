@@ -2,24 +2,26 @@
 // (set-up, every iteration of Algorithm 3, 4 or 5, the FP64 true-residual
 // checks and, in the refinement modes, the outer FP64 refinement loop).
 //
-// Mapping: warps own fixed 32-row tiles (tile t -> warp t mod #warps), lane k
-// of a tile owns row 32t+k in every phase, so all vector updates are
-// row-local and coalesced.  Inner products accumulate per thread in FP64,
-// are summed per CTA by a fixed butterfly tree and written as per-CTA
-// partials; after a grid barrier every CTA sums all partials in the same
-// order, so the scalars are bitwise identical in every CTA and no CTA ever
-// has to broadcast them.
+// Mapping: warps own 32-row tiles (statically tile t -> warp t mod #warps;
+// for matrices with heavy-tailed rows the warps claim tiles from a counter),
+// lane k of a tile owns row 32t+k in every phase, so all vector updates are
+// row-local and coalesced.  Inner products accumulate per lane (exact
+// integer windows in FP64, FP64 sums in the refinement modes), are summed
+// exactly per warp and per CTA into one record per CTA; after a grid barrier
+// every CTA sums all records in the same exact way, so the scalars are
+// bitwise identical in every CTA and no CTA ever has to broadcast them.
 //
 // p-BiCGSafe (Alg. 4) per iteration i, two grid barriers:
-//   phase A  load the partials of iteration i (issued first), compute A s_i
-//            for the warp's first tile while those loads are in flight
-//            (the overlap of the inner-product reduction with MV, Section 3),
-//            finish the reduction -> beta, alpha, zeta, eta, stop test;
-//            then for every tile: A s_i and the fused recurrences for
-//            p, o, u, q, w, t, z, y_{i+1}, x_{i+1}, r_{i+1}, the partial
-//            g' = zeta As + eta g and s' = s - alpha q; partials of
-//            (y,y) (y,r) (r*,r) (r*,t) (r,r).                    -- barrier
-//   phase C  A w_i and l = q - Aw, g_{i+1} = g' - alpha Aw, s_{i+1} = s' - g_{i+1};
+//   phase A  pull the records of iteration i towards L1, compute A s_i for
+//            the warp's first tile meanwhile (the overlap of the
+//            inner-product reduction with MV, Section 3), finish the
+//            reduction -> beta, alpha, zeta, eta, stop test; then for every
+//            tile: A s_i and the fused recurrences for p, o, u, q, w, t, z,
+//            y_{i+1}, x_{i+1}, r_{i+1}; A s_i is stored for phase C;
+//            partials of (y,y) (y,r) (r*,r) (r*,t) (r,r).          -- barrier
+//   phase C  A w_i; q = As + beta l, g' = zeta As + eta g, s' = s - alpha q
+//            (the same expressions as in phase A), l = q - Aw,
+//            g_{i+1} = g' - alpha Aw, s_{i+1} = s' - g_{i+1};
 //            partials of (s,s) (s,y) (s,r) (r*,s).                -- barrier
 // ssBiCGSafe2 (Alg. 3), three barriers: A: s = A r + partials of s; B: the
 // reduction (not overlapped) -> scalars, p, o, u; C: w = A u, t, z, y, x, r.
@@ -705,10 +707,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT yn = vfma(-al, w, vfma(ze, s, et * y));
                         x = vfma(al, p, x) + z;
                         const VT rn = vfma(-al, o, r) - yn;
-                        const VT gp = vfma(ze, As, et * g);
-                        const VT sa = vfma(-al, q, s);
                         Pv[row] = p; U[row] = u; W[row] = w; Tv[row] = t; Z[row] = z;
-                        Y[row] = yn; X[row] = x; R[row] = rn; L[row] = q; G[row] = gp; sNxt[row] = sa;
+                        Y[row] = yn; X[row] = x; R[row] = rn; O[row] = As;
                         qa_SB = yn;
                         qb_SB = yn;
                         qa_SE = yn;
@@ -731,9 +731,12 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
-                // phase C: A w_i; l_i, g_{i+1}, s_{i+1} and the products involving s_{i+1}
+                // phase C: A w_i; q_i (again), l_i, g_{i+1}, s_{i+1} and the products
+                // involving s_{i+1}.  A s_i crosses the barrier in o (unused by this
+                // method outside the replacement step), so that phase A stores one
+                // vector instead of q, g' and s'; the expressions are the same.
                 wa_init10(xv);
-                const VT* const vC[] = {L, G, sNxt, Y, R, RS};
+                const VT* const vC[] = {O, L, G, sCur, Y, R, RS};
                 ++n_spmv;
                 int64_t c0, c1;
                 unsigned* tcc;
@@ -755,12 +758,15 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     VT qa_SD = VT(0), qb_SD = VT(0);
                     VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
-                        const VT q = sm[lane], gp = sm[32 + lane], sa = sm[64 + lane];
+                        const VT As = sm[lane], lp = sm[32 + lane], gi = sm[64 + lane], si = sm[96 + lane];
+                        const VT q = vfma(be, lp, As);
+                        const VT gp = vfma(ze, As, et * gi);
+                        const VT sa = vfma(-al, q, si);
                         const VT l = q - Aw;
                         const VT g = vfma(-al, Aw, gp);
                         const VT s = sa - g;
                         L[row] = l; G[row] = g; sNxt[row] = s;
-                        const VT y = sm[96 + lane], r = sm[128 + lane], rs = sm[160 + lane];
+                        const VT y = sm[128 + lane], r = sm[160 + lane], rs = sm[192 + lane];
                         qa_SA = s;
                         qb_SA = s;
                         qa_SC = s;
