@@ -217,7 +217,9 @@ def cpu_sample(A, b, kind, iters):
 def reference_arm(a):
     A, b = make_workload()
     kind = a.kind
-    iters_full = 370  # iterations of one full p-BiCGSafe solve of this system (oracle, measured once)
+    # iterations of one full solve of this system to 1e-10 (the oracle's count with the true-residual
+    # restarts; the FP64 GPU solve reproduces it exactly)
+    iters_full = {"p-BiCGSafe": 428, "ssBiCGSafe2": 370, "p-BiCGSafe-rr": 407}.get(kind, 428)
     per = max(2, min(a.cpu_iters, 20))
     times = []
     for s in range(a.warmup + a.steps):
@@ -397,6 +399,8 @@ def main():
             dist.barrier()
         total_ms = t0.elapsed_time(t1)
         per = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]
+        # accuracy of the last solve against the exact solution of A x = A 1 (outside the timed region)
+        results[-1]["max_abs_err_vs_ones"] = float((xd - 1.0).abs().max().item())
         return total_ms, per, results
 
     if a.profile:
@@ -475,7 +479,8 @@ def main():
             rr = rs[-1]
             extras["%s_%s" % (kind, prec)] = {
                 "ms_per_solve": tm / 3, "iterations": rr["iterations"], "outer_steps": rr["outer_steps"],
-                "rel_res_true": rr["rel_res_true"], "status": rr["status_name"],
+                "rel_res_true": rr["rel_res_true"], "max_abs_err_vs_ones": rr["max_abs_err_vs_ones"],
+                "status": rr["status_name"],
                 "us_per_iter": 1e3 * tm / 3 / max(1, rr["iterations"])}
 
     line = None
@@ -497,7 +502,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "no flush: matrix (183 MB) and vectors (16 x 16.8 MB) exceed the 129 MB L2"},
                 "iterations": iters, "outer_steps": outer, "converged_all_steps": ok,
-                "rel_res_true": r0["rel_res_true"], "kernel_ms": kernel_ms,
+                "rel_res_true": r0["rel_res_true"], "max_abs_err_vs_ones": r0["max_abs_err_vs_ones"],
+                "kernel_ms": kernel_ms,
                 "us_per_iter": 1e3 * kernel_ms / max(1, iters),
                 "gb_per_s_per_iter": achieved_gbs,
                 "roofline": roofline,

@@ -290,6 +290,34 @@ def test_edge_cases(env):
     assert res["status"] == bcs.NOT_CONVERGED and res["iterations"] == 5 and np.all(np.isfinite(x))
 
 
+def test_failure_statuses_without_fault(env):
+    """Failure detection with host-injected faults only: an empty system, a NaN in b, and a
+    matrix whose products vanish each return their status (no trap, no hang), and the
+    context stays usable for the next solve."""
+    bcs, torch, orc = env
+    # n = 0
+    A0 = W.CSR(0, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    res, x, h, _ = _gpu_solve(bcs, torch, A0, np.zeros(0), "p-BiCGSafe")
+    assert res["status"] == 0 and res["iterations"] == 0
+    # NaN in b -> non-finite scalars reported
+    A = W.cd2d(16, 5.0)
+    b = W.rhs_ones(A)
+    b[7] = np.nan
+    for kind in ["ssBiCGSafe2", "p-BiCGSafe"]:
+        res, x, h, _ = _gpu_solve(bcs, torch, A, b, kind)
+        assert res["status"] == bcs.ERR_NONFINITE
+    # all-zero values (stored entries of value 0): (A r, A r) = 0 at i = 0 -> breakdown
+    Z = W.CSR(A.n, A.rowptr.copy(), A.col.copy(), np.zeros(A.nnz))
+    for kind in ["ssBiCGSafe2", "p-BiCGSafe"]:
+        res, x, h, _ = _gpu_solve(bcs, torch, Z, W.rhs_ones(A), kind)
+        assert res["status"] == bcs.ERR_BREAKDOWN
+        ref = orc.solve(Z, W.rhs_ones(A), kind=kind, tol=1e-10, maxit=100)
+        assert ref["status_name"] == res["status_name"]
+    # the context is still usable
+    res, x, h, _ = _gpu_solve(bcs, torch, A, W.rhs_ones(A), "p-BiCGSafe")
+    assert res["status"] == 0
+
+
 def test_determinism(env):
     """Same inputs, same launch configuration -> bitwise identical results."""
     bcs, torch, orc = env
