@@ -108,6 +108,7 @@ def args_parse():
     ap.add_argument("--workload", default="cd3d_128", choices=list(SIDE_WORKLOADS) + ["cd3d_128"],
                     help="cd3d_128 (the benchmark line); the others print a side measurement line")
     ap.add_argument("--tune", action="store_true", help="side workloads: autotune the layout / lanes per row first")
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi"], help="side workloads: preconditioner")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed solves (no end-to-end, side-by-side or CPU legs): the command profiled by ncu")
     return ap.parse_args()
@@ -256,7 +257,7 @@ def side_single(a, bcs, torch, dist, world, rank):
     else:
         layout, tpr = a.layout, a.tpr
     S = bcs.solver_create(M, a.kind, tol=1e-10, maxit=a.maxit, precision=a.precision, layout=layout,
-                          threads_per_row=tpr, max_outer=30)
+                          threads_per_row=tpr, max_outer=30, precond=a.precond)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
     for _ in range(a.warmup):
@@ -279,7 +280,8 @@ def side_single(a, bcs, torch, dist, world, rank):
             "us_per_iter": t * 1e6 / max(1, res["iterations"]), "status": res["status_name"],
             "rel_res_true": res["rel_res_true"],
             "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "n": A.n, "nnz": A.nnz,
-                       "kind": a.kind, "precision": a.precision, "layout": layout, "threads_per_row": tpr},
+                       "kind": a.kind, "precision": a.precision, "layout": layout, "threads_per_row": tpr,
+                       "precond": a.precond},
             "hbm": {"achieved": gbs, "peak": hp, "unit": "GB/s", "frac": gbs / hp, "peak_source": src},
             "tune": tune}
 

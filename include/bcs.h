@@ -54,6 +54,15 @@ enum { BCS_FP64 = 0, BCS_FP32_REFINE = 1, BCS_BF16MAT_REFINE = 2 };
  * BCS_LAYOUT_AUTO (solver option only): the layout bcs_autotune chose for the
  * matrix and precision, CSR if it was not tuned. */
 enum { BCS_LAYOUT_AUTO = 0, BCS_LAYOUT_CSR = 1, BCS_LAYOUT_SELL = 2 };
+/* Preconditioning (no counterpart in the paper, which uses none: Section 5).
+ * BCS_PRECOND_JACOBI: right preconditioning with D = diag(A): the solver runs
+ * on A D^-1 y = b (scaled copies of the matrix values, built at
+ * bcs_solver_create) and returns x = D^-1 y; x0 enters as y0 = D x0.  The
+ * residual of the solved system equals b - A x, so tol keeps its meaning.
+ * Requires every diagonal entry stored, nonzero and finite (else
+ * BCS_ERR_ARG at bcs_solver_create). */
+enum { BCS_PRECOND_NONE = 0, BCS_PRECOND_JACOBI = 1 };
+
 /* Value copies held on the device (bit mask; FP64 is always kept). */
 enum { BCS_STORE_F64 = 1, BCS_STORE_F32 = 2, BCS_STORE_BF16 = 4 };
 
@@ -89,7 +98,9 @@ typedef struct {
                              smallest recursive residual (default 20; 0 = off); the FP64 outer step
                              then recomputes the true residual and starts a fresh Krylov space */
     int tile_order;       /* single system: 0 = library choice, 1 = static (tile t to warp t mod warps),
-                             2 = dynamic (warps claim tiles from a counter); results do not depend on it */
+                             2 = dynamic (warps claim tiles from a counter); FP64 results do not depend on
+                             it, refinement-mode results may in the last bits */
+    int precond;          /* BCS_PRECOND_NONE (default) or BCS_PRECOND_JACOBI (single-system solves) */
 } bcs_options;
 
 typedef struct {

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("history_len", ctypes.c_int),
                 ("layout", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("max_ctas", ctypes.c_int), ("spin_budget_ms", ctypes.c_double), ("inner_maxit", ctypes.c_int),
-                ("inner_stall", ctypes.c_int), ("tile_order", ctypes.c_int)]
+                ("inner_stall", ctypes.c_int), ("tile_order", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -146,6 +146,8 @@ def options(**kw):
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "precond" and isinstance(v, str):
+            v = {"none": 0, "jacobi": 1}[v]
         if k == "layout" and isinstance(v, str):
             v = {"auto": LAYOUT_AUTO, "csr": LAYOUT_CSR, "sell": LAYOUT_SELL}[v]
         setattr(o, k, v)

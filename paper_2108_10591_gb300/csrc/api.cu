@@ -24,6 +24,8 @@ int dispatch_batched_f64(const BatchArgs* B, int tpr, int nclusters, cudaStream_
 int dispatch_batched_f32(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
 int dispatch_batched_bf16(const BatchArgs* B, int tpr, int nclusters, cudaStream_t st, int* max_clusters);
 int default_tpr(const bcs_matrix_s* A, int precision);
+int precond_setup(bcs_solver s);
+int precond_scale(bcs_solver s, double* x, int into, cudaStream_t st);
 }  // namespace bcs
 
 namespace {
@@ -91,6 +93,7 @@ int check_options(const bcs_options& o) {
     if (!(o.spin_budget_ms > 0.0)) return BCS_ERR_ARG;
     if (o.inner_maxit < 0 || o.inner_stall < 0) return BCS_ERR_ARG;
     if (o.tile_order < 0 || o.tile_order > 2) return BCS_ERR_ARG;
+    if (o.precond != BCS_PRECOND_NONE && o.precond != BCS_PRECOND_JACOBI) return BCS_ERR_ARG;
     return BCS_OK;
 }
 
@@ -133,7 +136,8 @@ const char* bcs_status_string(int s) {
 void bcs_solver_destroy(bcs_solver s) {
     if (!s) return;
     cudaDeviceSynchronize();
-    void* ptrs[] = {s->vecmem, s->x64w, s->b64w, s->partials, s->bar, s->hist, s->scal, s->out, s->xb_dev};
+    void* ptrs[] = {s->vecmem, s->x64w, s->b64w, s->partials, s->bar, s->hist, s->scal, s->out, s->xb_dev,
+                    s->pdiag, s->pval64, s->pvalin};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->host_out) cudaFreeHost(s->host_out);
@@ -211,6 +215,8 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (!rc && cudaMallocHost((void**)&s->host_out, sizeof(double) * NOUT + 64) != cudaSuccess) rc = BCS_ERR_OOM;
     if (!rc && (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess)) rc = BCS_ERR_CUDA;
     if (!rc && cudaMemset(s->partials, 0, sizeof(double) * 2 * (size_t)grid * NSLOT * kRec) != cudaSuccess) rc = BCS_ERR_CUDA;
+    s->precond = o.precond;
+    if (!rc && s->precond == BCS_PRECOND_JACOBI) rc = precond_setup(s);
     if (rc) {
         bcs_solver_destroy(s);
         return rc;
@@ -252,6 +258,10 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
         P->b64 = b;
     }
     P->val = inner_values(A, s->layout, s->valtype);
+    if (s->precond == BCS_PRECOND_JACOBI) {  // the solver runs on A D^-1
+        P->val64 = s->pval64;
+        P->val = s->valtype == VAL_F64 ? (const void*)s->pval64 : (const void*)s->pvalin;
+    }
     P->b = b;
     P->x = x;
     const size_t npad = (size_t)std::max<int64_t>(((A->n + 31) / 32) * 32, 32);
@@ -302,7 +312,10 @@ static int launch(bcs_solver s, const double* b, double* x, cudaStream_t st) {
     if (cudaMemsetAsync(s->bar, 0, 64, st) != cudaSuccess) return BCS_ERR_CUDA;
     if (cudaMemsetAsync(s->out, 0, sizeof(double) * NOUT, st) != cudaSuccess) return BCS_ERR_CUDA;
     cudaEventRecord(s->ev0, st);
+    // right preconditioning: the kernel iterates on y = D x
+    if (s->precond == BCS_PRECOND_JACOBI && precond_scale(s, x, 1, st) != 0) return BCS_ERR_CUDA;
     const int e = dispatch(&P, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, s->grid, st, nullptr);
+    if (e == 0 && s->precond == BCS_PRECOND_JACOBI && precond_scale(s, x, 0, st) != 0) return BCS_ERR_CUDA;
     cudaEventRecord(s->ev1, st);
     return e == 0 ? BCS_OK : BCS_ERR_CUDA;
 }
@@ -371,6 +384,7 @@ int bcs_batch_create(int nsys, const bcs_matrix* A, int kind, double tol, int ma
     o.layout = BCS_LAYOUT_CSR;
     int rc = check_options(o);
     if (rc) return rc;
+    if (o.precond != BCS_PRECOND_NONE) return BCS_ERR_ARG;  // batched solves are unpreconditioned
     int vt_f32 = 0, valtype = 0;
     int64_t maxn = 1;
     for (int k = 0; k < nsys; ++k) {

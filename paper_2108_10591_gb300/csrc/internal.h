@@ -135,6 +135,10 @@ struct bcs_solver_s {
     double* out = nullptr;
     double* host_out = nullptr;   // pinned copy of out
     double* xb_dev = nullptr;     // bcs_solve_host staging (2n doubles), allocated on first use
+    int precond = 0;              // BCS_PRECOND_*
+    double* pdiag = nullptr;      // Jacobi: diag(A) in the caller's row order
+    double* pval64 = nullptr;     // Jacobi: A D^-1 in the solver's layout, FP64
+    void* pvalin = nullptr;       // Jacobi: A D^-1 in the inner value type (refinement modes)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int hist_len = 0;
     int last_iters = 0;

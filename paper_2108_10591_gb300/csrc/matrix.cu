@@ -220,6 +220,14 @@ int spmv_launch(bcs_matrix A, int layout, const MT* val, const VT* x, VT* y, int
 }  // namespace
 
 namespace bcs {
+// value copies with the upload's roundings (used by the preconditioner's scaled copies)
+int convert_values(const double* in, int valtype, void* out, int64_t m, cudaStream_t st) {
+    if (m <= 0) return 0;
+    if (valtype == VAL_F32) k_to_f32<<<grid_for(m, 256), 256, 0, st>>>(in, (float*)out, m);
+    else if (valtype == VAL_BF16) k_to_bf16<<<grid_for(m, 256), 256, 0, st>>>(in, (uint16_t*)out, m);
+    else return (int)cudaMemcpyAsync(out, in, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    return (int)cudaGetLastError();
+}
 // Lanes per CSR row when the caller does not choose: the autotuned value for
 // the precision if there is one, else one lane per row (no cross-lane
 // reduction: on GB300 an FP64 shuffle-add costs an FP64-pipe slot like an FMA).
