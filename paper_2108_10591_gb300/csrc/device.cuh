@@ -111,40 +111,7 @@ template <> struct VecOf<double> { typedef double type; };
 __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 
-// ---- TMA bulk copies into shared memory with mbarrier completion ----------------------
-
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-// arrive (count 1) and announce `bytes` of transactions for the current phase
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-// bulk copy global -> this CTA's shared memory, completing on bar (16-byte aligned, size % 16 == 0)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-// order this thread's earlier generic-proxy accesses before later async-proxy (TMA) accesses
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
-// bounded wait for the completion of phase `parity` of bar; false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long budget) {
-    const long long t0 = clock64();
-    for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > budget) return false;
-    }
-}
 
 // Per-warp double-buffered staging of the 32-row chunks of up to kMaxStage
 // vectors.  Every lane copies its own row of each vector with cp.async
@@ -167,10 +134,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <class VT>
 struct WarpStager {
     VT* buf;                   // [2][kMaxStage][32] in shared memory
-    unsigned long long* bar;   // unused (kept for the layout)
-    unsigned parity;           // unused
     unsigned pending;          // bit s: stage s has a committed group not yet waited for
-    bool dead;                 // unused
 
     template <int K>
     __device__ __forceinline__ void issue(const VT* const (&v)[K], int64_t tile, int stage) {
@@ -181,16 +145,13 @@ struct WarpStager {
         pending |= 1u << stage;
     }
     // wait for `stage` (the older of the two in flight when `other` is pending)
-    __device__ __forceinline__ const VT* wait(int stage, long long, int*) {
+    __device__ __forceinline__ const VT* wait(int stage) {
         if ((pending >> (stage ^ 1)) & 1u) cp_async_wait<1>(); else cp_async_wait<0>();
         pending &= ~(1u << stage);
         return buf + stage * kMaxStage * 32;
     }
-    __device__ __forceinline__ void settle(long long, int*) {
-        cp_async_wait<0>();
-        pending = 0u;
-    }
-    __device__ __forceinline__ void drain(long long) {
+    // every copy in flight has landed (before the stages are abandoned or reused out of order)
+    __device__ __forceinline__ void settle() {
         cp_async_wait<0>();
         pending = 0u;
     }

@@ -254,13 +254,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     extern __shared__ __align__(128) unsigned char s_dyn[];
     WarpStager<VT> stg;
     stg.buf = (VT*)(s_dyn + (size_t)warp * 2 * kMaxStage * 32 * sizeof(VT));
-    stg.bar = (unsigned long long*)(s_dyn + (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT)) + 2 * warp;
-    stg.parity = 0u;
     stg.pending = 0u;
-    stg.dead = false;
 
-    // bounded wait for in-flight staging copies on an error exit (about 0.5 s)
-    constexpr long long kDrainBudget = 1000000000ll;
     // issue the warp's first two tiles of a phase (after the grid barrier that
     // made the previous phase's writes visible)
     // CSR with one lane per row, FP32 vectors: the row range of the lane's row
@@ -330,7 +325,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 P.b64w[row] = P.b[src];
             }
         }
-        if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+        if (!grp.sync(&s_flag)) { stg.settle(); return; }
     }
 
     int status = BCS_NOT_CONVERGED, inner_status = BCS_OK;
@@ -377,7 +372,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             flush_partials<(1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(xv, s_x,
                                                                                                     myrec(0));
             flush_partials<(1u << ST)>(xt, s_x, myrec(0));
-            if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+            if (!grp.sync(&s_flag)) { stg.settle(); return; }
             reduce_partials<10>(rbase(0), nblk, s_x, s_sum);
             ++n_spmv;
             ++n_red;
@@ -423,7 +418,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_acc(xv[SG], qa_SG, qb_SG, row < n);
             }
             flush_partials<(1u << SA) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(0));
-            if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+            if (!grp.sync(&s_flag)) { stg.settle(); return; }
         }
 
         // ---------------- iterations ----------------------------------------------------------
@@ -453,7 +448,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     if (kRp) rp_load(t1, rpa_n, rpb_n);
                     const VT sv = spmv_rp(R, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
-                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
+                    const VT* sm = stg.wait((int)(kt & 1));
                     const int64_t row = tile * 32 + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
@@ -480,7 +475,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     t1 = t2;
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(cur));
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
             } else {
                 // phase A: A s_i of the first tile is in flight while the partials of
                 // iteration i are reduced (the overlap of the reduction with MV, Section 3)
@@ -584,7 +579,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             __syncthreads();
             if (s_ctl[0]) {
                 // the run stops here: the staged first tiles of this phase A are not used
-                stg.settle(P.spin_budget, P.err);
+                stg.settle();
                 inner_status = s_ctl[1];
                 break;
             }
@@ -600,7 +595,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 for (int64_t kt = 0; b0 < ntiles; ++kt) {
                     const int64_t tile = b0;
                     const int64_t b2 = tiles_next(b1, tb);
-                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
+                    const VT* sm = stg.wait((int)(kt & 1));
                     const int64_t row = tile * 32 + lane;
                     if (row < n) {
                         const VT r = sm[lane], s = sm[32 + lane], t = sm[64 + lane], y = sm[96 + lane];
@@ -614,7 +609,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     b0 = b1;
                     b1 = b2;
                 }
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // phase C: w_i = A u_i; t_i, z_i, y_{i+1}, x_{i+1}, r_{i+1}
                 wa_init10(xv);
                 const VT* const vPC[] = {O, R, U, sCur, Y, Pv, RS, Z};
@@ -632,7 +627,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     if (kRp) rp_load(c1, rpa_n, rpb_n);
                     const VT w = spmv_rp(U, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
-                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
+                    const VT* sm = stg.wait((int)(kt & 1));
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
@@ -670,7 +665,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     c1 = c2;
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
             } else if (!rr_step) {
                 // phase A (continued): fused recurrences of Alg. 4
                 ++n_spmv;  // A s_i (its first tile already above)
@@ -685,7 +680,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     if (kRp && kt > 0) rp_load(pa1, rpa_n, rpb_n);
                     const VT As = (kt == 0) ? as_first : spmv_rp(sCur, tile, rpa, rpb);
                     if (kt > 0) { rpa = rpa_n; rpb = rpb_n; }
-                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
+                    const VT* sm = stg.wait((int)(kt & 1));
                     const int64_t row = tile * 32 + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
@@ -730,7 +725,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     pa1 = pa2;
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // phase C: A w_i; q_i (again), l_i, g_{i+1}, s_{i+1} and the products
                 // involving s_{i+1}.  A s_i crosses the barrier in o (unused by this
                 // method outside the replacement step), so that phase A stores one
@@ -751,7 +746,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     if (kRp) rp_load(c1, rpa_n, rpb_n);
                     const VT Aw = spmv_rp(W, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
-                    const VT* sm = stg.wait((int)(kt & 1), P.spin_budget, P.err);
+                    const VT* sm = stg.wait((int)(kt & 1));
                     const int64_t row = tile * 32 + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
@@ -785,7 +780,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     c1 = c2;
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
             } else {
                 // residual replacement iteration (Alg. 5)
@@ -800,7 +795,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         Pv[row] = p; O[row] = o; U[row] = u;
                     }
                 }
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // w_i = A u_i (q_i = A o_i is not used after a replacement); t, z, y_{i+1}, x_{i+1}
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT w = spmv(U, tile);
@@ -815,7 +810,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         W[row] = w; Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x;
                     }
                 }
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // r_{i+1} = b - A x_{i+1}; l_i = A t_i; g_{i+1} = A y_{i+1}
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -850,7 +845,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // s_{i+1} = A r_{i+1}
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -878,7 +873,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
-                if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+                if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 ++rr_steps;
                 n_spmv += 5;  // w = A u; A x, A t, A y; s = A r
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
@@ -892,7 +887,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 if (row < n) P.x64[row] += (double)X[row];
             }
         }
-        if (!grp.sync(&s_flag)) { stg.drain(kDrainBudget); return; }
+        if (!grp.sync(&s_flag)) { stg.settle(); return; }
     }
 
     if (rank == 0 && threadIdx.x == 0) {
@@ -923,10 +918,10 @@ __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_cons
     solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN>(P, grp);
 }
 
-// dynamic shared memory of the solver kernels: the per-warp staging buffers and their mbarriers
+// dynamic shared memory of the solver kernels: the per-warp staging buffers
 template <class VT, int NW>
 constexpr size_t stage_smem_bytes() {
-    return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT) + (size_t)NW * 2 * sizeof(unsigned long long);
+    return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT);
 }
 
 template <class VT, class MT, int LAYOUT, int T, bool DYN>
