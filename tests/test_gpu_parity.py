@@ -328,23 +328,23 @@ def test_determinism(env):
     assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("csize", [1, 2, 4])
 def test_batched(env, prec, csize):
     """Independent systems of uneven size in one launch (one cluster of csize CTAs per
-    system), each against its own oracle solve: FP64 bit-identical, FP32 + refinement to
-    the FP64 tolerance."""
+    system), each against its own oracle solve: FP64 bit-identical, FP32 and BF16-matrix
+    inner solves + FP64 refinement to the FP64 tolerance."""
     bcs, torch, orc = env
     mats, sides, betas = W.batch_cd2d(count=12, seed=11, kmin=8, kmax=40)
     Ms, bs, xs, refs = [], [], [], []
     for A in mats:
         b = W.rhs_ones(A)
-        Ms.append(bcs.csr_upload(A, stores=bcs.STORE_F32))
+        Ms.append(bcs.csr_upload(A, stores=bcs.STORE_F32 | bcs.STORE_BF16))
         bs.append(torch.from_numpy(b).cuda())
         xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
         refs.append(orc.solve(A, b, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=20, max_restarts=29))
     code, res = bcs.solve_batched(Ms, bs, xs, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, precision=prec, rr_m=20,
-                                  ctas_per_sm=csize)
+                                  ctas_per_sm=csize, max_outer=60)
     assert code == 0
     for A, b, x, r, ref in zip(mats, bs, xs, res, refs):
         xh = x.cpu().numpy()
@@ -494,6 +494,27 @@ def test_jacobi_right_preconditioning(env, cfg):
     M = bcs.csr_upload(Z)
     with pytest.raises(bcs.BcsError):
         bcs.solver_create(M, "p-BiCGSafe", precond="jacobi")
+
+
+def test_resume_from_x0_matches_oracle(env):
+    """Checkpoint / resume is a restart from x: a solve stopped after 40 iterations and
+    resumed from its x (passed back as x0) follows the oracle's run from the same x0 bit
+    for bit and reaches the tolerance."""
+    bcs, torch, orc = env
+    A = W.cd2d(48, 20.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    S1 = bcs.solver_create(M, "p-BiCGSafe", tol=1e-10, maxit=40, max_outer=1)
+    r1 = bcs.solve(S1, bd, x)
+    assert r1["status"] == bcs.NOT_CONVERGED and r1["iterations"] == 40
+    x0 = x.cpu().numpy().copy()
+    S2 = bcs.solver_create(M, "p-BiCGSafe", tol=1e-10, maxit=5000)
+    r2 = bcs.solve(S2, bd, x)
+    ref = orc.solve(A, b, x0=x0, kind="p-BiCGSafe", tol=1e-10, maxit=5000, max_restarts=29)
+    assert r2["status"] == 0 and r2["iterations"] == ref["iterations"]
+    assert np.array_equal(x.cpu().numpy(), ref["x"])
 
 
 def test_barrier_timeout_is_reported_and_recoverable(env):
