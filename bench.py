@@ -318,10 +318,15 @@ def side_batch(a, bcs, torch, dist, world, rank):
     t = max_over_ranks(statistics.mean(times), dist, "cuda")
     its = [r["iterations"] for r in res]
     ok = sum(1 for r in res if r["status"] == 0)
+    t0 = min(r["t_start"] for r in res)
+    spans = sorted(((r["t_end"] - r["t_start"]) * 1e-6, A.n) for r, A in zip(res, mats))
+    ends = sorted((r["t_end"] - t0) * 1e-6 for r in res)
     return {"metric": "solves/s", "value": 512 / t, "unit": "solves/s", "n_gpus": world, "ms_per_batch": t * 1e3,
             "systems": 512, "systems_this_rank": len(mats), "converged_this_rank": ok, "worst_status": code,
             "iterations": {"min": min(its), "median": float(np.median(its)), "max": max(its)},
             "max_rel_res_true": max(r["rel_res_true"] for r in res),
+            "per_system_ms": {"median": spans[len(spans) // 2][0], "max": spans[-1][0], "max_n": spans[-1][1],
+                              "last_finish": ends[-1], "p90_finish": ends[int(0.9 * (len(ends) - 1))]},
             "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "kind": a.kind,
                        "precision": a.precision, "batch_options": {k: kw[k] for k in kw
                                                                     if k in ("threads_per_row", "ctas_per_sm")},

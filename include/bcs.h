@@ -118,6 +118,8 @@ typedef struct {
                                  plus one per true-residual check) */
     int spmv_passes;          /* passes over the matrix (two per iteration, Table 1; plus set-up,
                                  true-residual checks and five per residual replacement) */
+    double t_start, t_end;    /* device clock (ns, %globaltimer) when the solve of this system started and
+                                 ended inside the kernel (batched solves: per system) */
 } bcs_result;
 
 /* Fill *opt with the defaults listed above. */

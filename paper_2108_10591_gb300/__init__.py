@@ -43,7 +43,8 @@ class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_steps", ctypes.c_int),
                 ("rr_steps", ctypes.c_int), ("fallbacks", ctypes.c_int), ("rel_res_recursive", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("r0_norm", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("grid_syncs", ctypes.c_int), ("reductions", ctypes.c_int), ("spmv_passes", ctypes.c_int)]
+                ("grid_syncs", ctypes.c_int), ("reductions", ctypes.c_int), ("spmv_passes", ctypes.c_int),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

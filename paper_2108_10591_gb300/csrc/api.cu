@@ -300,6 +300,8 @@ static int finish(bcs_solver s, cudaStream_t st, bcs_result* res) {
         res->grid_syncs = (int)o[O_SYNCS];
         res->reductions = (int)o[O_REDUCTIONS];
         res->spmv_passes = (int)o[O_SPMV];
+        res->t_start = o[O_T0];
+        res->t_end = o[O_T1];
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, s->ev0, s->ev1) == cudaSuccess) res->seconds = ms * 1e-3;
     }
@@ -568,6 +570,8 @@ int bcs_batch_solve(bcs_batch bt, const double* const* b, double* const* x, bcs_
             r.grid_syncs = (int)ob[O_SYNCS];
             r.reductions = (int)ob[O_REDUCTIONS];
             r.spmv_passes = (int)ob[O_SPMV];
+            r.t_start = ob[O_T0];
+            r.t_end = ob[O_T1];
             r.seconds = ms * 1e-3;
         }
     }

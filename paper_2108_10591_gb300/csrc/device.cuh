@@ -113,6 +113,13 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// device-wide nanosecond clock (the same on every SM)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Per-warp double-buffered staging of the 32-row chunks of up to kMaxStage
 // vectors.  Every lane copies its own row of each vector with cp.async
 // (global -> shared without going through registers, coalesced across the

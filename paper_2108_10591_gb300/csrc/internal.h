@@ -30,7 +30,7 @@ enum Vec { V_R = 0, V_RS, V_S, V_S2, V_Y, V_T, V_P, V_U, V_Z, V_W, V_L, V_G, V_O
 
 // Result block written by CTA 0 at the end of a solve (device memory).
 enum Out { O_STATUS = 0, O_ITERS, O_OUTER, O_RR, O_FALLBACK, O_RECREL, O_TRUEREL, O_R0, O_HISTLEN, O_SYNCS, O_REDUCTIONS,
-           O_SPMV, NOUT = 16 };
+           O_SPMV, O_T0, O_T1, NOUT = 16 };
 
 enum Layout { LAY_CSR = 0, LAY_SELL = 1 };
 enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };

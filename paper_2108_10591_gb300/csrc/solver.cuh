@@ -330,6 +330,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 
     int status = BCS_NOT_CONVERGED, inner_status = BCS_OK;
     int n_spmv = 0, n_red = 0;  // passes over the matrix and grid reductions (reported with the result)
+    const unsigned long long t_start = global_ns();
     grp.nsync = 0;
     int total = 0, evals = 0, runs = 0, hist_len = 0, rr_steps = 0, fallbacks = 0;
     double r0n = 0.0, thresh = 0.0, r0ref = 1.0, rtrue = 0.0, last_rec = 0.0;
@@ -903,6 +904,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         P.out[O_SYNCS] = grp.nsync;
         P.out[O_REDUCTIONS] = n_red;
         P.out[O_SPMV] = n_spmv;
+        P.out[O_T0] = (double)t_start;   // the system's start and end on the device clock (ns)
+        P.out[O_T1] = (double)global_ns();
     }
     if (P.perm != nullptr) {
         for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
