@@ -40,9 +40,9 @@ SM_MAX_MHZ = 2070.0
 # workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
 # iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
 # for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
-TRAFFIC = {"fp64": {"per_iter": 914.5e6, "per_outer": 1020.9e6},
-           "fp32": {"per_iter": 518.2e6, "per_outer": 827.3e6}}
-KERNEL_SHA = "2470f55de5877bb6"
+TRAFFIC = {"fp64": {"per_iter": 914.6e6, "per_outer": 1020.3e6},
+           "fp32": {"per_iter": 518.3e6, "per_outer": 825.8e6}}
+KERNEL_SHA = "52d8d78f2248b737"
 
 
 def kernel_sources_sha():
