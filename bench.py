@@ -29,7 +29,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-10 rel. residual, pipelined vs plain; HBM GB/s per iter; solves/s"
-WORKLOAD = "cd3d_128"
 HBM_PEAK_FALLBACK = 6800.0
 SMS = 152
 DFMA_PER_CLK_SM = 2          # GB300: FP64 FMA issue rate per SM per clock
@@ -112,6 +111,15 @@ def args_parse():
     ap.add_argument("--profile", action="store_true",
                     help="only the timed solves (no end-to-end, side-by-side or CPU legs): the command profiled by ncu")
     return ap.parse_args()
+
+
+def bench_config(a, n, nnz, world=1):
+    """The `config` of the benchmark line (the same for both arms)."""
+    return {"workload": "cd3d_%d: 3D -Lap u + 50(u_x+u_y+u_z), %d^3, 7-point upwind, n=%d, nnz=%d, "
+                        "b=A*1, x0=0" % (a.size, a.size, n, nnz),
+            "kind": a.kind, "precision": a.precision, "layout": a.layout, "tol": 1e-10,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "no flush: matrix (183 MB) and vectors (16 x 16.8 MB) exceed the 129 MB L2"}
 
 
 def make_workload(k=128):
@@ -216,7 +224,7 @@ def cpu_sample(A, b, kind, iters):
 
 
 def reference_arm(a):
-    A, b = make_workload()
+    A, b = make_workload(a.size)
     kind = a.kind
     # iterations of one full solve of this system to 1e-10 (the oracle's count with the true-residual
     # restarts; the FP64 GPU solve reproduces it exactly)
@@ -233,7 +241,7 @@ def reference_arm(a):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kind": kind, "precision": "fp64", "tol": 1e-10},
+            "config": bench_config(a, A.n, A.nnz),
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": "each step: %d iterations of the single-threaded FP64 oracle on the full "
                                        "system, scaled to one solve by %d iterations" % (per, iters_full)},
@@ -503,11 +511,7 @@ def main():
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[a.precision], "data": "synthetic",
-                "config": {"workload": "cd3d_%d: 3D -Lap u + 50(u_x+u_y+u_z), %d^3, 7-point upwind, n=%d, nnz=%d, "
-                                       "b=A*1, x0=0" % (a.size, a.size, n, nnz),
-                           "kind": a.kind, "precision": a.precision, "layout": a.layout, "tol": 1e-10,
-                           "parallelism": "replicas" if world > 1 else "single GPU",
-                           "l2": "no flush: matrix (183 MB) and vectors (16 x 16.8 MB) exceed the 129 MB L2"},
+                "config": bench_config(a, n, nnz, world),
                 "iterations": iters, "outer_steps": outer, "converged_all_steps": ok,
                 "rel_res_true": r0["rel_res_true"], "max_abs_err_vs_ones": r0["max_abs_err_vs_ones"],
                 "kernel_ms": kernel_ms,
