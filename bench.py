@@ -300,7 +300,7 @@ def side_batch(a, bcs, torch, dist, world, rank):
     order = sorted(range(len(mats)), key=lambda k: -(mats[k].nnz + mats[k].n))
     mine = [order[k] for k in shard_systems(len(order), rank, world)]
     mats = [mats[k] for k in mine]
-    Ms = [bcs.csr_upload(A, stores=bcs.STORE_F32) for A in mats]
+    Ms = [bcs.csr_upload(A, stores=bcs.STORE_F32 | bcs.STORE_BF16) for A in mats]
     kw = dict(precision=a.precision, max_outer=30)
     if a.kind == "p-BiCGSafe-rr":
         kw["rr_m"] = 20
