@@ -87,8 +87,10 @@ typedef struct {
     int history_len;      /* capacity of the residual history (default 4096 entries) */
     int layout;           /* BCS_LAYOUT_AUTO (default: tuned, else CSR), BCS_LAYOUT_CSR or BCS_LAYOUT_SELL
                              (must have been uploaded) */
-    int threads_per_row;  /* CSR only: 1, 4, 8 or 32 lanes per row; 0 = the library's choice (the tuned
-                             value, else 1) */
+    int threads_per_row;  /* CSR only: 1, 4, 8 or 32 lanes per row, or -1 = adaptive (one lane per row,
+                             the whole warp for rows of more than 32 entries); 0 = the library's choice
+                             (the tuned value, else -1 for heavy-tailed row lengths in the refinement
+                             modes, else 1: one lane per row keeps FP64 sums in plain row order) */
     int ctas_per_sm;      /* single system: CTAs per SM, 0 = by occupancy (one 24-warp CTA); batched
                              solves: CTAs per cluster (one cluster per system), 0 = 2; 1..8 */
     int max_ctas;         /* 0 = no cap; otherwise an upper bound on the grid size */
@@ -170,7 +172,7 @@ int bcs_matrix_export(bcs_matrix A, int32_t* rowptr, int32_t* col, double* val64
  *   store   BCS_STORE_F64 / F32 / BF16: which value copy to use.
  *   x, y    device vectors of n elements in original row order, FP64 when
  *           vec_f32 == 0, FP32 otherwise; x and y must not overlap.
- *   threads_per_row  CSR lanes per row (1, 4, 8, 32; 0 = automatic).
+ *   threads_per_row  CSR lanes per row (1, 4, 8, 32, or -1 = adaptive; 0 = automatic).
  * Rows are summed with fused multiply-adds; with one lane per row (and for
  * SELL) in storage order.  Asynchronous on stream.
  */

@@ -31,7 +31,7 @@ int precond_scale(bcs_solver s, double* x, int into, cudaStream_t st);
 namespace {
 
 // dynamic tile order exists for SELL and CSR with 1 or 8 lanes per row
-bool dyn_supported(int layout, int tpr) { return layout == LAY_SELL || tpr == 1 || tpr == 8; }
+bool dyn_supported(int layout, int tpr) { return layout == LAY_SELL || tpr == 1 || tpr == 8 || tpr == -1; }
 
 int dispatch(const KParams* P, int vt_f32, int valtype, int layout, int tpr, int dyn, int grid, cudaStream_t st,
              int* mg) {
@@ -52,7 +52,8 @@ int dispatch_b(const BatchArgs* B, int vt_f32, int valtype, int tpr, int nc, cud
     return dispatch_batched_bf16(B, tpr, nc, st, mc);
 }
 
-bool valid_tpr(int t) { return t == 1 || t == 4 || t == 8 || t == 32; }
+// lanes per CSR row: 1, 4, 8, 32, or -1 = adaptive (one lane per row, the whole warp for long rows)
+bool valid_tpr(int t) { return t == 1 || t == 4 || t == 8 || t == 32 || t == -1; }
 
 long long budget_cycles(double ms) {
     // SM cycles per millisecond at the GB300's maximum SM clock (2070 MHz);
@@ -648,7 +649,7 @@ int bcs_autotune(bcs_matrix A, int kind, int precision, int iters, bcs_tune_entr
     if (iters <= 0) iters = 20;
     std::vector<bcs_tune_entry> cand;
     if (A->layouts & BCS_LAYOUT_CSR)
-        for (int t : {1, 4, 8, 32}) cand.push_back({BCS_LAYOUT_CSR, t, 0, 0.0});
+        for (int t : {1, 4, 8, 32, -1}) cand.push_back({BCS_LAYOUT_CSR, t, 0, 0.0});
     if (A->layouts & BCS_LAYOUT_SELL) cand.push_back({BCS_LAYOUT_SELL, 1, 0, 0.0});
     TuneVecs v;
     rc = v.init(A->n);

@@ -255,6 +255,69 @@ __device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, c
     return acc;
 }
 
+// CSR tile with adaptive lanes per row (T == 0): a row of at most kLongRow
+// entries is summed by its own lane in storage order (as csr_tile<.., 1>);
+// each longer row is summed by the whole warp (lane l takes entries l, l+32,
+// ... in order, then a butterfly), so a tile with a few long rows no longer
+// waits for them one entry at a time.  The long rows' sums are therefore in a
+// different order than a plain sequential loop (deterministic).
+constexpr int kLongRow = 32;
+template <class VT, class MT>
+__device__ __forceinline__ VT csr_tile_adaptive(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                const MT* __restrict__ val, const VT* x, int64_t row0, int64_t n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = row0 + lane;
+    int rp0 = 0, rp1 = 0;
+    if (row < n) {
+        rp0 = __ldg(rowptr + row);
+        rp1 = __ldg(rowptr + row + 1);
+    }
+    const bool lng = rp1 - rp0 > kLongRow;
+    unsigned lmask = __ballot_sync(kFull, lng);
+    const int send = lng ? rp0 : rp1;
+    VT acc = VT(0);
+    for (int k0 = rp0; k0 < send; k0 += kSpmvBatch) {
+        int c[kSpmvBatch];
+        VT v[kSpmvBatch], xv[kSpmvBatch];
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j) {
+            const bool in = k0 + j < send;
+            c[j] = in ? __ldg(col + k0 + j) : 0;
+            v[j] = in ? (VT)ldv(val + k0 + j) : VT(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + j < send) ? x[c[j]] : VT(0);
+#pragma unroll
+        for (int j = 0; j < kSpmvBatch; ++j)
+            if (k0 + j < send) acc = vfma(v[j], xv[j], acc);
+    }
+    while (lmask) {
+        const int src = __ffs(lmask) - 1;
+        lmask &= lmask - 1u;
+        const int b = __shfl_sync(kFull, rp0, src), e = __shfl_sync(kFull, rp1, src);
+        VT part = VT(0);
+        for (int k0 = b + lane; k0 < e; k0 += 32 * 4) {
+            int c[4];
+            VT v[4], xv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool in = k0 + 32 * j < e;
+                c[j] = in ? __ldg(col + k0 + 32 * j) : 0;
+                v[j] = in ? (VT)ldv(val + k0 + 32 * j) : VT(0);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xv[j] = (k0 + 32 * j < e) ? x[c[j]] : VT(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (k0 + 32 * j < e) part = vfma(v[j], xv[j], part);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+        if (lane == src) acc = part;
+    }
+    return acc;
+}
+
 // CSR tile, one lane per row, with the lane's row range [rp0, rp1) already
 // loaded (rows >= n: an empty range): the same entries, order and fmas as
 // csr_tile<VT, MT, 1>.
@@ -284,7 +347,8 @@ __device__ __forceinline__ VT tile_spmv(const KParams& P, const MT* val, const V
     if constexpr (LAYOUT == LAY_SELL) {
         return sell_tile<VT, MT>(P.slice_ptr, P.col, val, x, tile);
     } else {
-        return csr_tile<VT, MT, T>(P.rowptr, P.col, val, x, tile * 32, P.n, s_buf);
+        if constexpr (T == 0) return csr_tile_adaptive<VT, MT>(P.rowptr, P.col, val, x, tile * 32, P.n);
+        else return csr_tile<VT, MT, T>(P.rowptr, P.col, val, x, tile * 32, P.n, s_buf);
     }
 }
 

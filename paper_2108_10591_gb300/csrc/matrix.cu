@@ -208,6 +208,7 @@ int spmv_launch(bcs_matrix A, int layout, const MT* val, const VT* x, VT* y, int
         P.rowptr = A->rowptr;
         P.col = A->col;
         switch (tpr) {
+            case -1: k_spmv<VT, MT, LAY_CSR, 0><<<grid, 256, 0, st>>>(P, val, x, y); break;
             case 1: k_spmv<VT, MT, LAY_CSR, 1><<<grid, 256, 0, st>>>(P, val, x, y); break;
             case 4: k_spmv<VT, MT, LAY_CSR, 4><<<grid, 256, 0, st>>>(P, val, x, y); break;
             case 8: k_spmv<VT, MT, LAY_CSR, 8><<<grid, 256, 0, st>>>(P, val, x, y); break;
@@ -229,10 +230,15 @@ int convert_values(const double* in, int valtype, void* out, int64_t m, cudaStre
     return (int)cudaGetLastError();
 }
 // Lanes per CSR row when the caller does not choose: the autotuned value for
-// the precision if there is one, else one lane per row (no cross-lane
-// reduction: on GB300 an FP64 shuffle-add costs an FP64-pipe slot like an FMA).
+// the precision if there is one, else adaptive for heavy-tailed row lengths in
+// the refinement modes, else one lane per row (no cross-lane reduction: on
+// GB300 an FP64 shuffle-add costs an FP64-pipe slot like an FMA).
 int default_tpr(const bcs_matrix_s* A, int precision) {
     if (precision >= 0 && precision < 3 && A->tuned_tpr[precision]) return A->tuned_tpr[precision];
+    // heavy-tailed row lengths in the refinement modes: adaptive (the warp takes
+    // the long rows together).  FP64 keeps one lane per row, whose sums follow
+    // the plain row order (bit-identical to a sequential FP64 solve).
+    if (precision != BCS_FP64 && (double)A->max_row > 4.0 * A->avg_row + 4.0 && A->max_row > kLongRow) return -1;
     return 1;
 }
 }  // namespace bcs
@@ -391,7 +397,7 @@ int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int ve
     int tpr = threads_per_row ? threads_per_row
                               : default_tpr(A, !vec_f32 ? BCS_FP64 : store == BCS_STORE_BF16 ? BCS_BF16MAT_REFINE
                                                                                               : BCS_FP32_REFINE);
-    if (tpr != 1 && tpr != 4 && tpr != 8 && tpr != 32) return BCS_ERR_ARG;
+    if (tpr != 1 && tpr != 4 && tpr != 8 && tpr != 32 && tpr != -1) return BCS_ERR_ARG;
     if (A->n == 0) return BCS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const bool sell = layout == BCS_LAYOUT_SELL;

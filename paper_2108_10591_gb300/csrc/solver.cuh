@@ -955,9 +955,9 @@ int max_grid_one(int* grid) {
 
 // Dispatch over layout and lanes-per-row for one (VT, MT) pair; each
 // translation unit instantiates one subset (SUBSET 0: SELL and CSR with 1 lane
-// per row, SUBSET 1: CSR with 4, 8 or 32 lanes per row, both in the static
-// tile order; SUBSET 2: the dynamic tile order for SELL and CSR with 1 or 8
-// lanes per row).
+// per row, SUBSET 1: CSR with 4, 8 or 32 lanes per row or adaptive (-1), both
+// in the static tile order; SUBSET 2: the dynamic tile order for SELL and CSR
+// with 1, 8 or adaptive lanes per row).
 template <class VT, class MT, int SUBSET>
 int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
 #define BCS_CASE(LAY, TT, D)                                                              \
@@ -967,6 +967,7 @@ int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, i
         BCS_CASE(LAY_CSR, 1, false);
     } else if constexpr (SUBSET == 1) {
         switch (tpr) {
+            case -1: BCS_CASE(LAY_CSR, 0, false);
             case 4: BCS_CASE(LAY_CSR, 4, false);
             case 8: BCS_CASE(LAY_CSR, 8, false);
             default: BCS_CASE(LAY_CSR, 32, false);
@@ -974,6 +975,7 @@ int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, i
     } else {
         if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1, true); }
         if (tpr == 8) { BCS_CASE(LAY_CSR, 8, true); }
+        if (tpr == -1) { BCS_CASE(LAY_CSR, 0, true); }
         BCS_CASE(LAY_CSR, 1, true);
     }
 #undef BCS_CASE
