@@ -116,21 +116,25 @@ __device__ __forceinline__ void flush_partials(ACC (&a)[10], XStage<NW>& st, uns
 // so 2^17 of them cannot overflow), then a warp sum and one rounding.
 // reduce_issue pulls the slot's records into L1 ahead of reduce_finish, so
 // that the caller can overlap that memory round trip with other work.
-template <int NS, int NW>
+// OFF: slot k is taken by warp k + OFF (warps below OFF are left free for
+// other work); OFF + NS <= NW or OFF = 0.
+template <int NS, int NW, int OFF = 0>
 __device__ __forceinline__ void reduce_issue(const unsigned long long* base, int nblk) {
     static_assert(NS >= 1 && NS <= 10, "slots");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    static_assert(OFF == 0 || OFF + NS <= NW, "offset slots must fit");
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - OFF;
+    if (warp < 0) return;
     for (int k = warp; k < NS; k += NW)
         for (int c = lane; c < nblk; c += 32)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(base + k * kRec + (size_t)c * NSLOT * kRec));
 }
 
-template <int NS, int NW>
+template <int NS, int NW, int OFF = 0>
 __device__ __forceinline__ void reduce_finish(const unsigned long long* base, int nblk, XStage<NW>& st, double* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - OFF;
     (void)st;
 #pragma unroll 1
-    for (int k = warp; k < NS; k += NW) {
+    for (int k = (warp < 0 ? NS : warp); k < NS; k += NW) {
         const unsigned long long* rk = base + k * kRec;
         int E = kXaEmpty;
         for (int c = lane; c < nblk; c += 32) {
@@ -217,6 +221,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     const int rank = grp.rank;
     const int kind = P.kind;
     const bool mixed = P.mixed != 0;
+    // with enough warps the grid reduction leaves warp 0 (the scalar recurrence)
+    // and warp 10 (the square root) free
+    constexpr int kRedOff = NW >= 11 ? 1 : 0;
+    constexpr int kSqrtWarp = NW >= 11 ? 10 : 1;
 
     VT* const R = (VT*)P.vec[V_R];
     VT* const RS = (VT*)P.vec[V_RS];
@@ -429,6 +437,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
             typename DotAccOf<VT>::type xv[10];
             VT as_first = VT(0);
+            bool first_late = false;   // this warp's first-tile SpMV runs in the scalar section
             int64_t pa0 = 0, pa1 = 0;   // p-BiCGSafe phase A: the warp's first two tiles
             unsigned* pac = nullptr;
             if (kind == BCS_SSBICGSAFE2) {
@@ -481,12 +490,17 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase A: A s_i of the first tile is in flight while the partials of
                 // iteration i are reduced (the overlap of the reduction with MV, Section 3)
                 if (!rr_step) {
-                    reduce_issue<9, NW>(rbase(cur), nblk);   // records travel to L1 during the SpMV
+                    // warps 1..9 reduce the nine slots while the others start their
+                    // first tile's SpMV; warps 1..9 start theirs while warp 0 forms
+                    // the scalars (so the reduction and the scalar recurrence both
+                    // run under the SpMV's memory latency)
+                    reduce_issue<9, NW, kRedOff>(rbase(cur), nblk);   // records travel to L1
                     const VT* const vA0[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
                     tiles_begin(pa0, pa1, pac);
                     stage_two(vA0, pa0, pa1);
-                    if (pa0 < ntiles) as_first = spmv(sCur, pa0);
-                    reduce_finish<9, NW>(rbase(cur), nblk, s_x, s_sum);
+                    first_late = kRedOff > 0 && warp >= kRedOff && warp < kRedOff + 9;
+                    if (!first_late && pa0 < ntiles) as_first = spmv(sCur, pa0);
+                    reduce_finish<9, NW, kRedOff>(rbase(cur), nblk, s_x, s_sum);
                 } else {
                     reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
                 }
@@ -516,9 +530,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     dv = den;
                 }
                 s_q[lane] = num / dv;
-            } else if (warp == 1 && lane == 0) {
+            } else if (warp == kSqrtWarp && lane == 0) {
                 s_q[4] = sqrt(s_sum[SR]);
             }
+            if (first_late && pa0 < ntiles) as_first = spmv(sCur, pa0);
             __syncthreads();
             if (threadIdx.x == 0) {
                 const double a = s_sum[SA], bb = s_sum[SB], c = s_sum[SC];
