@@ -174,7 +174,9 @@ int bcs_matrix_export(bcs_matrix A, int32_t* rowptr, int32_t* col, double* val64
  *           vec_f32 == 0, FP32 otherwise; x and y must not overlap.
  *   threads_per_row  CSR lanes per row (1, 4, 8, 32, or -1 = adaptive; 0 = automatic).
  * Rows are summed with fused multiply-adds; with one lane per row (and for
- * SELL) in storage order.  Asynchronous on stream.
+ * SELL) in storage order.  Asynchronous on stream.  The SELL path permutes x
+ * and y through a scratch buffer owned by A, so SELL calls on one matrix
+ * must not run concurrently on different streams.
  */
 int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int vec_f32,
              int threads_per_row, void* stream);

@@ -1,4 +1,5 @@
 // C ABI: solver objects, single and batched solves, status strings.
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -153,7 +154,7 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (!A || kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR || !(tol >= 0.0) || maxit < 0) return BCS_ERR_ARG;
     bcs_options o;
     if (opt) o = *opt; else bcs_options_default(&o);
-    if (o.rr_M == 0) o.rr_M = maxit + 1;
+    if (o.rr_M == 0) o.rr_M = maxit < INT_MAX ? maxit + 1 : maxit;  // 0 = no limit below maxit
     int rc = check_options(o);
     if (rc) return rc;
     if (o.layout == BCS_LAYOUT_AUTO) {
@@ -383,7 +384,7 @@ int bcs_batch_create(int nsys, const bcs_matrix* A, int kind, double tol, int ma
     if (kind < BCS_SSBICGSAFE2 || kind > BCS_P_BICGSAFE_RR || !(tol >= 0.0) || maxit < 0) return BCS_ERR_ARG;
     bcs_options o;
     if (opt) o = *opt; else bcs_options_default(&o);
-    if (o.rr_M == 0) o.rr_M = maxit + 1;
+    if (o.rr_M == 0) o.rr_M = maxit < INT_MAX ? maxit + 1 : maxit;  // 0 = no limit below maxit
     o.layout = BCS_LAYOUT_CSR;
     int rc = check_options(o);
     if (rc) return rc;

@@ -262,6 +262,8 @@ int bcs_csr_upload(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t*
     bcs_matrix A = new bcs_matrix_s();
     int64_t* rp64 = nullptr;
     int* flags = nullptr;  // [0] bad, [1] max row length
+    int32_t* inv = nullptr;    // SELL build: inverse permutation
+    int64_t* width = nullptr;  // SELL build: padded entries per slice
     int hflags[2] = {0, 0};
     const int64_t m = std::max<int64_t>(nnz, 1);
     A->n = n;
@@ -299,8 +301,6 @@ int bcs_csr_upload(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t*
         k_to_bf16<<<grid_for(m, 256), 256, 0, st>>>(A->val64, A->valbf16, nnz);
     }
     if (layouts & BCS_LAYOUT_SELL) {
-        int32_t* inv = nullptr;
-        int64_t* width = nullptr;
         const int64_t ns = (n + 31) / 32;
         A->sell_C = 32;
         A->sell_sigma = sell_sigma;
@@ -339,15 +339,14 @@ int bcs_csr_upload(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t*
                                                             n, ns, nullptr, A->svalbf16);
             }
         }
-        CK(cudaStreamSynchronize(st));
-        cudaFree(inv);
-        cudaFree(width);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
 done:
     if (rp64) cudaFree(rp64);
     if (flags) cudaFree(flags);
+    if (inv) cudaFree(inv);
+    if (width) cudaFree(width);
     if (rc != BCS_OK) {
         bcs_matrix_free(A);
         return rc;

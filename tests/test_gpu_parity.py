@@ -310,6 +310,10 @@ def test_edge_cases(env):
     # maxit reached -> not converged, x finite
     res, x, h, _ = _gpu_solve(bcs, torch, W.cd2d(64, 20.0), W.rhs_ones(W.cd2d(64, 20.0)), "p-BiCGSafe", maxit=5)
     assert res["status"] == bcs.NOT_CONVERGED and res["iterations"] == 5 and np.all(np.isfinite(x))
+    # the largest iteration limit (the default replacement limit M = maxit must not overflow)
+    A = W.cd2d(16, 5.0)
+    res, x, h, _ = _gpu_solve(bcs, torch, A, W.rhs_ones(A), "p-BiCGSafe-rr", maxit=2**31 - 1)
+    assert res["status"] == 0 and res["rel_res_true"] <= 1e-10
 
 
 def test_failure_statuses_without_fault(env):
