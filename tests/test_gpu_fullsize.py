@@ -86,3 +86,108 @@ def test_powerlaw_4m_fp32_refinement(env):
         res = bcs.solve(S, bd, x)
         assert res["status"] == 0
         assert orc.true_residual(A, b, x.cpu().numpy()) / np.linalg.norm(b) <= 1e-10
+
+
+# ---- 27-point 192^3 stencil (n = 7,077,888, nnz = 189,119,224): CSR and SELL-C-sigma ----------
+
+@pytest.fixture(scope="module")
+def cd3d27(env):
+    bcs, torch, orc = env
+    A = W.cd3d27(192, 100.0)
+    M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL, sell_sigma=256,
+                       stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    return A, M
+
+
+def _row_abs_sums(orc, A, x):
+    """sum_j |a_ij x_j| per row, by the oracle's SpMV on |A| and |x|."""
+    return orc.spmv(W.CSR(A.n, A.rowptr, A.col, np.abs(A.val)), np.abs(x))
+
+
+def test_cd3d27_192_format_build_bit_exact(env, cd3d27):
+    """The full-size CSR copy, its FP32 / BF16 roundings and the SELL-32-256 arrays equal
+    the oracle's, bit for bit."""
+    bcs, torch, orc = env
+    A, M = cd3d27
+    E = bcs.matrix_export(M, csr=True, f32=True, bf16=True, sell=True)
+    assert np.array_equal(E["rowptr"], A.rowptr.astype(np.int32))
+    assert np.array_equal(E["col"], A.col)
+    assert np.array_equal(E["val64"].view(np.uint64), A.val.view(np.uint64))
+    assert np.array_equal(E["val32"].view(np.uint32), A.val.astype(np.float32).view(np.uint32))
+    assert np.array_equal(E["valbf16"], orc.to_bf16_bits(A.val))
+    del E["val32"], E["valbf16"], E["val64"], E["col"]
+    S = orc.sell_build(A, 32, 256)
+    assert np.array_equal(E["perm"], S["perm"])
+    assert np.array_equal(E["slice_ptr"], S["slice_ptr"])
+    assert np.array_equal(E["scol"], S["col"])
+    assert np.array_equal(E["sval64"].view(np.uint64), S["val"].view(np.uint64))
+
+
+def test_cd3d27_192_spmv_all_stores(env, cd3d27):
+    """y = A x at full size: FP64 with one lane per row and SELL bit-identical to the oracle's
+    sequential row sums; FP32 and BF16 value copies within the FP32 accumulation bound of the
+    exact product of the stored values."""
+    bcs, torch, orc = env
+    A, M = cd3d27
+    x = np.random.default_rng(5).standard_normal(A.n)
+    want = orc.spmv(A, x)
+    xd = torch.from_numpy(x).cuda()
+    for lay, tpr in [(bcs.LAYOUT_CSR, 1), (bcs.LAYOUT_SELL, 0)]:
+        yd = torch.full_like(xd, np.nan)
+        bcs.spmv(M, xd, yd, layout=lay, threads_per_row=tpr)
+        assert np.array_equal(yd.cpu().numpy(), want), (lay, tpr)
+    del xd, yd
+    x32 = x.astype(np.float32)
+    xd = torch.from_numpy(x32).cuda()
+    lens = np.diff(A.rowptr)
+    for store in [bcs.STORE_F32, bcs.STORE_BF16]:
+        if store == bcs.STORE_F32:
+            vals = A.val.astype(np.float32).astype(np.float64)
+        else:
+            vals = (orc.to_bf16_bits(A.val).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        Ar = W.CSR(A.n, A.rowptr, A.col, vals)
+        exact = orc.spmv(Ar, x32.astype(np.float64))
+        bound = _row_abs_sums(orc, Ar, x32.astype(np.float64)) * (lens + 1) * 2.0 ** -24
+        for lay, tpr in [(bcs.LAYOUT_CSR, 1), (bcs.LAYOUT_SELL, 0)]:
+            yd = torch.zeros_like(xd)
+            bcs.spmv(M, xd, yd, layout=lay, store=store, threads_per_row=tpr)
+            y = yd.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(y - exact) <= bound + 1e-30), (store, lay, tpr)
+
+
+@pytest.mark.parametrize("kind,prec,layout", [("p-BiCGSafe", "fp32", "csr"), ("p-BiCGSafe", "fp32", "sell"),
+                                              ("p-BiCGSafe-rr", "fp64", "csr"), ("ssBiCGSafe2", "fp64", "sell")])
+def test_cd3d27_192_full_solve_true_residual(env, cd3d27, kind, prec, layout):
+    """Full solves of the 27-point system to 1e-10, the true residual of the returned x
+    recomputed by the oracle."""
+    bcs, torch, orc = env
+    A, M = cd3d27
+    b = W.rhs_ones(A)
+    S = bcs.solver_create(M, kind, tol=1e-10, maxit=20000, precision=prec, layout=layout, max_outer=60)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    assert res["status"] == 0
+    rel = orc.true_residual(A, b, x.cpu().numpy()) / np.linalg.norm(b)
+    assert rel <= 1e-10
+    assert abs(rel - res["rel_res_true"]) <= 1e-3 * rel + 1e-16
+
+
+# ---- 512 independent 2D systems, sides 32..256, in one persistent launch -------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_cd2d_512_true_residuals(env, prec):
+    """The full 512-system batch with the default batched options: every system converges and
+    its true residual, recomputed by the oracle, meets 1e-10."""
+    bcs, torch, orc = env
+    mats, sides, betas = W.batch_cd2d()
+    Ms = [bcs.csr_upload(A, stores=bcs.STORE_F32) for A in mats]
+    bs = [W.rhs_ones(A) for A in mats]
+    bd = [torch.from_numpy(b).cuda() for b in bs]
+    xd = [torch.zeros_like(b) for b in bd]
+    worst, res = bcs.solve_batched(Ms, bd, xd, kind="p-BiCGSafe-rr", tol=1e-10, maxit=20000, precision=prec,
+                                   max_outer=60)
+    assert worst == 0
+    assert all(r["status"] == 0 for r in res)
+    for A, b, x in zip(mats, bs, xd):
+        assert orc.true_residual(A, b, x.cpu().numpy()) / np.linalg.norm(b) <= 1e-10
