@@ -1,5 +1,5 @@
 // Device building blocks: memory-ordering primitives, the bounded grid
-// barrier, deterministic block reductions, and the 32-row-tile SpMV used by
+// barrier, per-warp asynchronous staging, and the 32-row-tile SpMV used by
 // every solver phase ("MV" in Section 3 / Table 1).
 #pragma once
 #include <cuda_runtime.h>
@@ -64,39 +64,6 @@ struct GridBarrier {
     }
 };
 
-// ---- reductions --------------------------------------------------------------
-
-// Butterfly sum over the warp: every lane ends with the bitwise-same value
-// (each step adds two identical operand pairs in commuted order).
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    return v;
-}
-
-// Deterministic block sum of K values per thread.  Result in out[0..K) (shared
-// memory, visible to all threads after return).  scratch: kWarps*K doubles.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch, double* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) scratch[warp * K + k] = v[k];
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double t = lane < kWarps ? scratch[lane * K + k] : 0.0;
-            t = warp_sum(t);
-            if (lane == 0) out[k] = t;
-        }
-    }
-    __syncthreads();
-}
-
 // ---- value types ---------------------------------------------------------------
 
 __device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
@@ -105,9 +72,6 @@ __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const uint16_t* p) {
     return __uint_as_float(((unsigned)__ldg((const unsigned short*)p)) << 16);
 }
-template <class MT> struct VecOf { typedef float type; };
-template <> struct VecOf<double> { typedef double type; };
-
 __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 

@@ -64,7 +64,7 @@ struct KParams {
     const double* b64;
     double* b64w;           // SELL: writable permuted copy of b
     void* vec[NVEC];
-    double* partials;       // exact partial records: [2][CTAs][NSLOT][3] 64-bit words
+    double* partials;       // exact partial records: [2][CTAs][NSLOT][kRec = 4] 64-bit words
     unsigned* bar;          // barrier counter, zero at launch
     unsigned* tilectr;      // two tile counters (dynamic tile order), zero at launch; nullptr: static order
     int* err;               // error flag, zero at launch

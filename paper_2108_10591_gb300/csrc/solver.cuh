@@ -12,10 +12,11 @@
 // bitwise identical in every CTA and no CTA ever has to broadcast them.
 //
 // p-BiCGSafe (Alg. 4) per iteration i, two grid barriers:
-//   phase A  pull the records of iteration i towards L1, compute A s_i for
-//            the warp's first tile meanwhile (the overlap of the
-//            inner-product reduction with MV, Section 3), finish the
-//            reduction -> beta, alpha, zeta, eta, stop test; then for every
+//   phase A  warps 1-9 pull the records of iteration i towards L1 and sum
+//            them while the other warps compute A s_i for their first tile
+//            (the overlap of the inner-product reduction with MV, Section 3);
+//            warp 0 forms beta, alpha, zeta, eta and the stop test while
+//            warps 1-9 compute their first tile's A s_i; then for every
 //            tile: A s_i and the fused recurrences for p, o, u, q, w, t, z,
 //            y_{i+1}, x_{i+1}, r_{i+1}; A s_i is stored for phase C;
 //            partials of (y,y) (y,r) (r*,r) (r*,t) (r,r).          -- barrier
@@ -264,8 +265,6 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     stg.buf = (VT*)(s_dyn + (size_t)warp * 2 * kMaxStage * 32 * sizeof(VT));
     stg.pending = 0u;
 
-    // issue the warp's first two tiles of a phase (after the grid barrier that
-    // made the previous phase's writes visible)
     // CSR with one lane per row, FP32 vectors: the row range of the lane's row
     // in the warp's next tile is loaded one tile ahead, so the SpMV of a tile
     // starts with its column and value loads (in FP64 mode the two extra
@@ -510,8 +509,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
 
             // ---- scalar recurrence and stop test (Alg. 3/4 i = 0 branch and general case) ----
             // The independent quotients are formed side by side by the lanes of
-            // warp 0 (one division sequence) while warp 1 takes the square root;
-            // thread 0 then finishes alpha and the bookkeeping.  Every value is
+            // warp 0 (one division sequence) while warp kSqrtWarp takes the square
+            // root; thread 0 then finishes alpha and the bookkeeping.  Every value is
             // the same IEEE quotient of the same operands as in a sequential
             // evaluation.
             if (warp == 0 && lane < 4) {
