@@ -39,9 +39,9 @@ SM_MAX_MHZ = 2070.0
 # workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
 # iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
 # for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
-TRAFFIC = {"fp64": {"per_iter": 914.6e6, "per_outer": 1021.2e6},
-           "fp32": {"per_iter": 518.4e6, "per_outer": 824.5e6}}
-KERNEL_SHA = "6f5dfc92f9923db0"
+TRAFFIC = {"fp64": {"per_iter": 914.5e6, "per_outer": 1021.9e6},
+           "fp32": {"per_iter": 518.3e6, "per_outer": 826.1e6}}
+KERNEL_SHA = "83110cb593661e40"
 
 
 def kernel_sources_sha():
