@@ -36,6 +36,8 @@
 #pragma once
 #include <math.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 #include "xacc.cuh"
 
@@ -245,6 +247,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     VT* const X = mixed ? (VT*)P.vec[V_D] : (VT*)(void*)P.x64;
     const VT* const Bin = mixed ? (const VT*)BinW : (const VT*)(const void*)P.b64;
     const MT* const val = (const MT*)P.val;
+    // row index inside a tile loop: 32-bit with FP32 vectors (fewer address
+    // instructions per tile, measured faster); 64-bit with FP64 vectors, where
+    // the 32-bit form was measured slower.  n < 2^31 (checked at upload).
+    using RowT = typename std::conditional<sizeof(VT) == 4, int, int64_t>::type;
     VT* const sbuf = s_buf[warp];
     double* const sbuf64 = s_buf64[warp];
 
@@ -325,7 +331,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     // ---- SELL: the solve runs in the permuted row order ----
     if (P.perm != nullptr) {
         for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-            const int64_t row = tile * 32 + lane;
+            const RowT row = (RowT)(tile * 32) + lane;
             if (row < n) {
                 const int32_t src = __ldg(P.perm + row);
                 P.x64[row] = P.x[src];
@@ -354,7 +360,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             wa_init10(xt);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const double ax = spmv64(P.x64, tile);
-                const int64_t row = tile * 32 + lane;
+                const RowT row = (RowT)(tile * 32) + lane;
                 double qa_ST = double(0), qb_ST = double(0);
                 VT qa_SF = VT(0), qb_SF = VT(0);
                 if (row < n) {
@@ -407,7 +413,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             ++n_spmv;
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const VT sv = spmv(R, tile);
-                const int64_t row = tile * 32 + lane;
+                const RowT row = (RowT)(tile * 32) + lane;
                 VT qa_SA = VT(0), qb_SA = VT(0);
                 VT qa_SD = VT(0), qb_SD = VT(0);
                 VT qa_SG = VT(0), qb_SG = VT(0);
@@ -458,7 +464,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const VT sv = spmv_rp(R, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1));
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
                     VT qa_SD = VT(0), qb_SD = VT(0);
@@ -611,7 +617,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t tile = b0;
                     const int64_t b2 = tiles_next(b1, tb);
                     const VT* sm = stg.wait((int)(kt & 1));
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     if (row < n) {
                         const VT r = sm[lane], s = sm[32 + lane], t = sm[64 + lane], y = sm[96 + lane];
                         VT p = sm[128 + lane], u = sm[160 + lane];
@@ -643,7 +649,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const VT w = spmv_rp(U, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1));
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
                     VT qa_SF = VT(0), qb_SF = VT(0);
@@ -696,7 +702,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const VT As = (kt == 0) ? as_first : spmv_rp(sCur, tile, rpa, rpb);
                     if (kt > 0) { rpa = rpa_n; rpb = rpb_n; }
                     const VT* sm = stg.wait((int)(kt & 1));
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
                     VT qa_SF = VT(0), qb_SF = VT(0);
@@ -762,7 +768,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const VT Aw = spmv_rp(W, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1));
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
                     VT qa_SD = VT(0), qb_SD = VT(0);
@@ -800,7 +806,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             } else {
                 // residual replacement iteration (Alg. 5)
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     if (row < n) {
                         const VT r = R[row], s = sCur[row], t = Tv[row], y = Y[row];
                         VT p = Pv[row], u = U[row];
@@ -814,7 +820,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // w_i = A u_i (q_i = A o_i is not used after a replacement); t, z, y_{i+1}, x_{i+1}
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT w = spmv(U, tile);
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     if (row < n) {
                         const VT o = O[row], r = R[row], u = U[row], s = sCur[row], y = Y[row], p = Pv[row];
                         VT z = Z[row], x = X[row];
@@ -832,7 +838,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const VT ax = spmv(X, tile);
                     const VT at = spmv(Tv, tile);
                     const VT ay = spmv(Y, tile);
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
                     VT qa_SF = VT(0), qb_SF = VT(0);
@@ -865,7 +871,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const VT s = spmv(R, tile);
-                    const int64_t row = tile * 32 + lane;
+                    const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
                     VT qa_SD = VT(0), qb_SD = VT(0);
@@ -898,7 +904,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         // refinement: x += d in FP64 (not after a non-finite inner run)
         if (mixed && inner_status != BCS_ERR_NONFINITE) {
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                const int64_t row = tile * 32 + lane;
+                const RowT row = (RowT)(tile * 32) + lane;
                 if (row < n) P.x64[row] += (double)X[row];
             }
         }
@@ -923,7 +929,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     }
     if (P.perm != nullptr) {
         for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-            const int64_t row = tile * 32 + lane;
+            const RowT row = (RowT)(tile * 32) + lane;
             if (row < n) P.x[__ldg(P.perm + row)] = P.x64[row];
         }
     }

@@ -358,32 +358,11 @@ struct DAcc {
 };
 __device__ __forceinline__ void wa_init(DAcc& a) { a.s = 0.0; }
 
-// FP32 -> FP64 widening done entirely with integer operations (the FP64 pipe
-// stays free for the fma): rebias the exponent and move the fraction;
-// subnormals are normalised, zero, infinities and NaNs keep their class.
-// A pure function of its operand, so the widening of a value that enters
-// several inner products is computed once.
-__device__ __forceinline__ double widen(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned sgn = u & 0x80000000u;
-    const unsigned ex = (u >> 23) & 0xFFu;
-    const unsigned m = u & 0x7FFFFFu;
-    unsigned hi, lo;
-    if (ex != 0u) {
-        const unsigned dex = (ex == 0xFFu) ? 0x7FFu : ex + 896u;
-        hi = sgn | (dex << 20) | (m >> 3);
-        lo = m << 29;
-    } else if (m != 0u) {
-        const int pmsb = 31 - __clz((int)m);                   // 0..22
-        const unsigned mm = (m << (23 - pmsb)) & 0x7FFFFFu;  // fraction after the leading one
-        hi = sgn | ((unsigned)(pmsb + 874) << 20) | (mm >> 3);
-        lo = mm << 29;
-    } else {
-        hi = sgn;
-        lo = 0u;
-    }
-    return __hiloint2double((int)hi, (int)lo);
-}
+// FP32 -> FP64 widening (exact).  The conversion instruction was measured
+// faster than rebiasing the bits with integer operations (fewer issued
+// instructions per tile).  A pure function of its operand, so the widening of
+// a value that enters several inner products is computed once.
+__device__ __forceinline__ double widen(float f) { return (double)f; }
 __device__ __forceinline__ void wa_acc(DAcc& a, float x, float y, bool valid) {
     if (valid) a.s = fma(widen(x), widen(y), a.s);
 }
