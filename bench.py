@@ -39,9 +39,9 @@ SM_MAX_MHZ = 2070.0
 # workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
 # iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
 # for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
-TRAFFIC = {"fp64": {"per_iter": 914.5e6, "per_outer": 1021.9e6},
-           "fp32": {"per_iter": 518.3e6, "per_outer": 826.1e6}}
-KERNEL_SHA = "83110cb593661e40"
+TRAFFIC = {"fp64": {"per_iter": 914.7e6, "per_outer": 1019.7e6},
+           "fp32": {"per_iter": 518.2e6, "per_outer": 824.4e6}}
+KERNEL_SHA = "ab3cd972aad23f61"
 
 
 def kernel_sources_sha():
