@@ -381,6 +381,29 @@ def test_batched(env, prec, csize):
         assert np.max(np.abs(xh - 1.0)) <= 1e-6
 
 
+@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe"])
+def test_batched_degenerate_systems(env, kind):
+    """A batch mixing an empty system, a 1x1 system, a tiny random nonsymmetric one, a ragged
+    49-row grid and a 256-row grid: the empty one converges at once, every other one is
+    bit-identical (status, iterations, x) to its own FP64 oracle solve."""
+    bcs, torch, orc = env
+    empty = W.CSR(0, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    mats = [W.cd2d(7, 3.0), empty, W.dense_to_csr(np.array([[4.0]])), W.tiny_random(5, 3), W.cd2d(16, 9.0)]
+    Ms = [bcs.csr_upload(A) for A in mats]
+    bs_h = [W.rhs_ones(A) if A.n else np.zeros(0) for A in mats]
+    bs = [torch.from_numpy(b).cuda() for b in bs_h]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device="cuda") for A in mats]
+    code, res = bcs.solve_batched(Ms, bs, xs, kind=kind, tol=1e-10, maxit=500, max_outer=30)
+    assert res[1]["status"] == 0 and res[1]["iterations"] == 0
+    for A, b, x, r in zip(mats, bs_h, xs, res):
+        if A.n == 0:
+            continue
+        ref = orc.solve(A, b, kind=kind, tol=1e-10, maxit=500, max_restarts=29)
+        assert r["iterations"] == ref["iterations"], (A.n, r, ref["iterations"])
+        assert np.array_equal(x.cpu().numpy(), ref["x"]), A.n
+        assert (r["status"] == 0) == (ref["status_name"] == "ok"), (A.n, r["status"], ref["status_name"])
+
+
 def test_batch_handle_replays_with_new_vectors(env):
     """bcs_batch: the systems fixed once, solved three times with new right-hand sides and
     new x buffers (the first solve captures the launch sequence, the others replay it);
