@@ -256,7 +256,8 @@ int bcs_solve_host(bcs_solver s, const double* b_host, double* x_host, bcs_resul
 int bcs_get_history(bcs_solver s, double* out, int cap, int* len);
 int bcs_get_scalars(bcs_solver s, double* out, int cap, int* len);
 
-/* Free a solver (NULL is ignored). */
+/* Free a solver (NULL is ignored).  Waits for the device first (a solve still
+ * in flight on any stream finishes before its workspace is released). */
 void bcs_solver_destroy(bcs_solver s);
 
 /*
@@ -306,7 +307,8 @@ typedef struct {
  * Autotuner (no counterpart in the paper).  Times `iters` iterations (0 = 20)
  * of the persistent solver of method `kind` in `precision` (tolerance 0, one
  * run, b = ones, x0 = 0) for every candidate the matrix supports: CSR with 1,
- * 4, 8 and 32 lanes per row, and SELL-C-sigma if uploaded; each candidate
+ * 4, 8 or 32 lanes per row or adaptive lanes (-1), and SELL-C-sigma if
+ * uploaded; each candidate
  * is run twice and the second run timed.  The fastest is recorded in A for
  * that precision: solvers created later with layout BCS_LAYOUT_AUTO and
  * threads_per_row 0 use it, and bcs_spmv uses its lanes per row.

@@ -28,7 +28,8 @@ OK, NOT_CONVERGED, ERR_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_NONFINITE,
 EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_matrix_export", "bcs_spmv", "bcs_dot", "bcs_dot_noalloc",
             "bcs_matrix_free", "bcs_solver_create", "bcs_solve", "bcs_solve_host", "bcs_get_history",
             "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_batch_create", "bcs_batch_solve",
-            "bcs_batch_destroy", "bcs_autotune", "bcs_batch_autotune", "bcs_status_string"]
+            "bcs_batch_destroy", "bcs_autotune", "bcs_batch_autotune", "bcs_status_string",
+            "bcs_autotune_sell_sigma"]
 
 
 class Options(ctypes.Structure):
@@ -92,6 +93,7 @@ def _load():
     L.bcs_autotune.argtypes = [P, I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(TuneEntry), P]
     L.bcs_batch_autotune.argtypes = [I, P, I, ctypes.POINTER(Options), I, P, I, ctypes.POINTER(I),
                                      ctypes.POINTER(Options), P]
+    L.bcs_autotune_sell_sigma.argtypes = [P, I, I, I, P, I, P, ctypes.POINTER(I), ctypes.POINTER(P), P]
     L.bcs_status_string.argtypes = [I]
     L.bcs_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -372,6 +374,23 @@ def autotune(M, kind="p-BiCGSafe", precision="fp64", iters=20, stream=None):
     _check(lib.bcs_autotune(M.handle, k, _precision(precision), int(iters), ctypes.cast(E, ctypes.c_void_p), 8,
                             ctypes.byref(cnt), ctypes.byref(best), _stream(stream)), "bcs_autotune")
     return best.as_dict(), [E[i].as_dict() for i in range(min(cnt.value, 8))]
+
+
+def autotune_sell_sigma(M, kind="p-BiCGSafe", precision="fp64", sigmas=(32, 128, 256, 1024, 4096), iters=20,
+                        tuned=True, stream=None):
+    """bcs_autotune_sell_sigma: times the SELL layout built with each sorting window sigma, on copies of M
+    (M itself is not modified).  Returns (best sigma, {sigma: us per iteration}, a new Matrix with M's
+    layouts and the SELL layout at the best sigma, or None when tuned is False)."""
+    sig = np.ascontiguousarray(sigmas, dtype=np.int32)
+    us = np.zeros(len(sig), dtype=np.float64)
+    best = ctypes.c_int()
+    h = ctypes.c_void_p()
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib.bcs_autotune_sell_sigma(M.handle, k, _precision(precision), int(iters), sig.ctypes.data, len(sig),
+                                       us.ctypes.data, ctypes.byref(best), ctypes.byref(h) if tuned else None,
+                                       _stream(stream)), "bcs_autotune_sell_sigma")
+    T = Matrix(h.value, M.n, M.nnz) if tuned else None
+    return best.value, {int(s_): float(t) for s_, t in zip(sig, us)}, T
 
 
 def batch_autotune(Ms, kind="p-BiCGSafe", iters=20, stream=None, **kw):

@@ -381,6 +381,36 @@ def test_batched(env, prec, csize):
         assert np.max(np.abs(xh - 1.0)) <= 1e-6
 
 
+def test_sell_sigma_autotune(env):
+    """bcs_autotune_sell_sigma: every candidate window is timed, the caller's matrix keeps its
+    SELL arrays, the returned matrix holds the oracle's SELL build at the chosen sigma (bit for
+    bit), and a FP64 SELL solve on it is bit-identical to the oracle."""
+    bcs, torch, orc = env
+    A = W.powerlaw(n=20001, seed=9)
+    M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL, sell_sigma=256, stores=bcs.STORE_F32)
+    before = bcs.matrix_export(M, csr=False, sell=True)
+    best, times, T = bcs.autotune_sell_sigma(M, "p-BiCGSafe-rr", "fp32", sigmas=(32, 256, 1024), iters=10)
+    assert best in (32, 256, 1024) and sorted(times) == [32, 256, 1024]
+    assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+    after = bcs.matrix_export(M, csr=False, sell=True)
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    E = bcs.matrix_export(T, csr=True, sell=True)
+    S = orc.sell_build(A, 32, best)
+    assert np.array_equal(E["col"], A.col)
+    assert np.array_equal(E["perm"], S["perm"]) and np.array_equal(E["slice_ptr"], S["slice_ptr"])
+    assert np.array_equal(E["scol"], S["col"])
+    assert np.array_equal(E["sval64"].view(np.uint64), S["val"].view(np.uint64))
+    b = W.rhs_ones(A)
+    St = bcs.solver_create(T, "p-BiCGSafe-rr", tol=1e-10, maxit=5000, layout="sell", rr_m=10)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    r = bcs.solve(St, bd, xd)
+    ref = orc.solve(A, b, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=10, max_restarts=29)
+    assert r["status"] == 0 and r["iterations"] == ref["iterations"]
+    assert np.array_equal(xd.cpu().numpy(), ref["x"])
+
+
 @pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe"])
 def test_batched_degenerate_systems(env, kind):
     """A batch mixing an empty system, a 1x1 system, a tiny random nonsymmetric one, a ragged

@@ -20,9 +20,14 @@ def bcs():
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "bcs.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(bcs_[a-z_0-9]+)\s*\(", src)))
+    """Every bcs_* function that a header under include/ declares."""
+    syms = set()
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", name)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            syms.update(re.findall(r"\b(bcs_[a-z_0-9]+)\s*\(", src))
+    return sorted(syms)
 
 
 def test_header_declares_the_boundary():
@@ -76,5 +81,8 @@ def test_argument_checks_without_gpu(bcs):
     assert lib.bcs_solve_batched(-1, None, 0, 1e-8, 10, None, None, None, None, None) == bcs.ERR_ARG
     assert lib.bcs_solve_batched(0, None, 0, 1e-8, 10, None, None, None, None, None) == bcs.OK
     assert lib.bcs_solve_batched(1, None, 7, 1e-8, 10, None, None, None, None, None) == bcs.ERR_ARG
+    sig = (ctypes.c_int * 2)(32, 256)
+    best = ctypes.c_int()
+    assert lib.bcs_autotune_sell_sigma(None, 1, 0, 10, sig, 2, None, ctypes.byref(best), None, None) == bcs.ERR_ARG
     lib.bcs_matrix_free(None)
     lib.bcs_solver_destroy(None)
