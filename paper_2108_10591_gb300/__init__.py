@@ -1,13 +1,14 @@
-"""Thin Python binding of libbcs.so (include/bcs.h).
+"""Thin Python binding of libbcs.so (include/bcs.h, include/bcs_tune.h).
 
 Argument marshalling only: every step of a solve runs in the library's CUDA
 kernels.  Device vectors are passed as torch CUDA tensors (their data_ptr())
 or raw integer device pointers; host arrays as numpy arrays.  Import fails
 loudly when the compiled library is missing: there is no CPU fallback.
 
-Names follow the C ABI: csr_upload, matrix_info, matrix_export, spmv,
-solver_create, solve, solve_host, get_history, get_scalars, solve_batched,
-status_string.
+Names follow the C ABI: csr_upload, matrix_info, matrix_export, spmv, dot,
+dot_noalloc, solver_create, solve, solve_host, get_history, get_scalars,
+solve_batched, Batch (bcs_batch_*), autotune, batch_autotune,
+autotune_sell_sigma, status_string.
 """
 import ctypes
 import os
