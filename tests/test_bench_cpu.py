@@ -37,3 +37,22 @@ def test_solve_work_adds_outer_step_set_up():
     assert f2 > f1 and b2 > b1
     assert f1 >= 100 * bench.flops_per_iter("p-BiCGSafe", N, NNZ)
     assert b1 >= 100 * bench.bytes_per_iter("p-BiCGSafe", N, NNZ)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints the contract's JSON line;
+    run here on a 16^3 grid so that it takes a second."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--size", "16",
+                          "--steps", "1", "--warmup", "0", "--cpu-iters", "5"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("cd3d_16:")
