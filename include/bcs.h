@@ -80,7 +80,8 @@ enum {
 
 typedef struct {
     int rr_m;             /* Alg. 5 replacement epoch m (default 100; Section 5.2 uses 100 and 96) */
-    int rr_M;             /* Alg. 5 replacement limit M: replace only while i < M (default: maxit) */
+    int rr_M;             /* Alg. 5 replacement limit M: replace only while i < M (0, the default:
+                             M = maxit + 1, no limit within the iteration budget) */
     int precision;        /* BCS_FP64 (default) | BCS_FP32_REFINE | BCS_BF16MAT_REFINE */
     double inner_tol;     /* refinement modes: inner stop at ||r_inner|| <= inner_tol*||r_outer|| (default 1e-2) */
     int max_outer;        /* outer steps: true-residual checks / restarts / refinement steps (default 30) */
