@@ -369,11 +369,11 @@ def main():
             reference_arm(a)
         return
     import torch
+    torch.cuda.set_device(local)   # before the process group: NCCL binds this rank to its GPU
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
     import paper_2108_10591_gb300 as bcs
 
     if a.workload != "cd3d_128":
