@@ -130,6 +130,24 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _dvec(t, n, name, dtypes=("float64",)):
+    """Check a device vector argument before its pointer reaches the library: a torch tensor must
+    live on the GPU, be contiguous, have one of `dtypes` and n elements (n=None: any).  A raw integer
+    device pointer is passed through unchecked.  A host tensor here would otherwise be read by a
+    kernel as device memory."""
+    if t is None or isinstance(t, int):
+        return
+    if not getattr(t, "is_cuda", False):
+        raise ValueError("%s must be a CUDA tensor (got %s)" % (name, type(t).__name__))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    dt = str(t.dtype).replace("torch.", "")
+    if dt not in dtypes:
+        raise ValueError("%s must have dtype %s (got %s)" % (name, " or ".join(dtypes), dt))
+    if n is not None and t.numel() != n:
+        raise ValueError("%s must have %d elements (got %d)" % (name, n, t.numel()))
+
+
 def _np(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
@@ -229,6 +247,8 @@ def matrix_export(M, csr=True, f32=False, bf16=False, sell=False):
 def spmv(M, x, y, layout=LAYOUT_CSR, store=STORE_F64, threads_per_row=0, stream=None):
     """bcs_spmv: y = A x on the device (x, y torch CUDA tensors, float64 or float32)."""
     import torch
+    _dvec(x, M.n, "x", ("float64", "float32"))
+    _dvec(y, M.n, "y", (str(x.dtype).replace("torch.", ""),))
     f32 = x.dtype == torch.float32
     _check(lib.bcs_spmv(M.handle, layout, store, _ptr(x), _ptr(y), int(f32), threads_per_row, _stream(stream)),
            "bcs_spmv")
@@ -238,6 +258,8 @@ def spmv(M, x, y, layout=LAYOUT_CSR, store=STORE_F64, threads_per_row=0, stream=
 def dot(x, y, stream=None):
     """bcs_dot: correctly rounded (x, y) of two torch CUDA tensors (float64 or float32)."""
     import torch
+    _dvec(x, None, "x", ("float64", "float32"))
+    _dvec(y, x.numel(), "y", (str(x.dtype).replace("torch.", ""),))
     out = ctypes.c_double()
     _check(lib.bcs_dot(x.numel(), _ptr(x), _ptr(y), int(x.dtype == torch.float32), ctypes.byref(out),
                        _stream(stream)), "bcs_dot")
@@ -248,6 +270,9 @@ def dot_noalloc(x, y, out, stream=None):
     """bcs_dot_noalloc: (x, y) of two torch CUDA tensors into the one-element float64 CUDA
     tensor `out`, asynchronously, with no device allocation."""
     import torch
+    _dvec(x, None, "x", ("float64", "float32"))
+    _dvec(y, x.numel(), "y", (str(x.dtype).replace("torch.", ""),))
+    _dvec(out, 1, "out")
     _check(lib.bcs_dot_noalloc(x.numel(), _ptr(x), _ptr(y), int(x.dtype == torch.float32), _ptr(out),
                                _stream(stream)), "bcs_dot_noalloc")
     return out
@@ -278,6 +303,8 @@ def solver_create(M, kind="p-BiCGSafe", tol=1e-10, maxit=10000, **kw):
 
 def solve(S, b, x, stream=None):
     """bcs_solve with device vectors b, x (x holds x_0 on entry). Returns the result as a dict."""
+    _dvec(b, S.M.n, "b")
+    _dvec(x, S.M.n, "x")
     r = Result()
     code = lib.bcs_solve(S.handle, _ptr(b), _ptr(x), ctypes.byref(r), _stream(stream))
     if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
@@ -315,6 +342,11 @@ def get_scalars(S):
 def solve_batched(Ms, bs, xs, kind="p-BiCGSafe", tol=1e-10, maxit=10000, stream=None, **kw):
     """bcs_solve_batched: lists of matrices and device vectors. Returns (worst status, list of result dicts)."""
     n = len(Ms)
+    if len(bs) != n or len(xs) != n:
+        raise ValueError("one b and one x per system")
+    for k, (m, b, x) in enumerate(zip(Ms, bs, xs)):
+        _dvec(b, m.n, "b[%d]" % k)
+        _dvec(x, m.n, "x[%d]" % k)
     opts = options(**kw)
     H = (ctypes.c_void_p * n)(*[m.handle for m in Ms])
     B = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
@@ -350,6 +382,9 @@ class Batch:
         n = len(self.Ms)
         if len(bs) != n or len(xs) != n:
             raise ValueError("one b and one x per system")
+        for k, (m, b, x) in enumerate(zip(self.Ms, bs, xs)):
+            _dvec(b, m.n, "b[%d]" % k)
+            _dvec(x, m.n, "x[%d]" % k)
         B = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
         X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
         R = (Result * n)()

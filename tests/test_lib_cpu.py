@@ -86,3 +86,14 @@ def test_argument_checks_without_gpu(bcs):
     assert lib.bcs_autotune_sell_sigma(None, 1, 0, 10, sig, 2, None, ctypes.byref(best), None, None) == bcs.ERR_ARG
     lib.bcs_matrix_free(None)
     lib.bcs_solver_destroy(None)
+
+
+def test_host_tensors_are_refused_before_the_library(bcs):
+    """A CPU tensor passed where the library expects device memory is refused by the binding
+    (its pointer would otherwise be read by a kernel as a device address)."""
+    torch = pytest.importorskip("torch")
+    x = torch.ones(8, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        bcs.dot(x, x)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        bcs.dot_noalloc(x, x, torch.zeros(1, dtype=torch.float64))
