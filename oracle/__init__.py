@@ -43,13 +43,14 @@ class _Result(ctypes.Structure):
                 ("r0_norm", ctypes.c_double)]
 
 
-_LIB = None
+_LIBS = {}
 
 
-def lib():
-    global _LIB
-    if _LIB is None:
-        path = _build.build()
+def lib(parallel=False):
+    """The oracle library: the single-threaded parity build, or (parallel=True) the same source
+    built with OpenMP, used only to time the CPU baseline on every host core."""
+    if parallel not in _LIBS:
+        path = _build.build(parallel=parallel)
         L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         L.orc_spmv.argtypes = [ctypes.c_int64, P, P, P, P, P]
@@ -66,8 +67,8 @@ def lib():
         L.orc_sell_build.restype = ctypes.c_int64
         L.orc_to_bf16.argtypes = [ctypes.c_int64, P, P]
         L.orc_to_bf16.restype = None
-        _LIB = L
-    return _LIB
+        _LIBS[parallel] = L
+    return _LIBS[parallel]
 
 
 def _p(a):
@@ -81,20 +82,20 @@ def _csr(A):
     return rp, ci, va
 
 
-def spmv(A, x):
+def spmv(A, x, parallel=False):
     """y = A x (rows summed sequentially with fma)."""
     rp, ci, va = _csr(A)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.zeros(A.n, dtype=np.float64)
-    lib().orc_spmv(A.n, _p(rp), _p(ci), _p(va), _p(x), _p(y))
+    lib(parallel).orc_spmv(A.n, _p(rp), _p(ci), _p(va), _p(x), _p(y))
     return y
 
 
-def dot(x, y):
-    """Pairwise-summed inner product."""
+def dot(x, y, parallel=False):
+    """Correctly rounded inner product (exact sum of exact products, rounded once)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
-    return lib().orc_dot(len(x), _p(x), _p(y))
+    return lib(parallel).orc_dot(len(x), _p(x), _p(y))
 
 
 def true_residual(A, b, x):
@@ -105,7 +106,7 @@ def true_residual(A, b, x):
 
 
 def solve(A, b, x0=None, kind="p-BiCGSafe", tol=1e-10, maxit=10000, rr_m=100, rr_M=None,
-          max_restarts=0, hist_cap=None, dump_iter=-1, dump_phase=0):
+          max_restarts=0, hist_cap=None, dump_iter=-1, dump_phase=0, parallel=False):
     """Run Algorithm 3/4/5 (see bicgsafe_oracle.c).  Returns a dict with x,
     hist (sqrt(r_i)/||r_0|| per stop test), scalars (alpha, beta, zeta, eta per
     iteration of the first run), result fields and, when dump_iter >= 0, the
@@ -123,7 +124,7 @@ def solve(A, b, x0=None, kind="p-BiCGSafe", tol=1e-10, maxit=10000, rr_m=100, rr
     res = _Result()
     state = np.zeros(len(SV) * max(n, 1)) if dump_iter >= 0 else None
     sdump = np.zeros(len(SC)) if dump_iter >= 0 else None
-    st = lib().orc_solve(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), ctypes.byref(o), _p(hist), cap,
+    st = lib(parallel).orc_solve(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), ctypes.byref(o), _p(hist), cap,
                          ctypes.byref(hl), _p(scal), None if state is None else _p(state),
                          None if sdump is None else _p(sdump), ctypes.byref(res))
     out = dict(x=x, hist=hist[:hl.value].copy(), status=st, status_name=STATUS.get(st, str(st)),

@@ -45,6 +45,19 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/*
+ * Every loop over rows below is free of cross-row dependences.  The parity
+ * build compiles this file without OpenMP and runs them in order; the
+ * all-cores timing build (-fopenmp, the CPU baseline only) splits them over
+ * threads.  Both give identical bits: each row is computed by the same
+ * statements, and an inner product is the exact sum of exact products
+ * (per-thread exact partial sums merged exactly) rounded once.
+ */
+#define ORC_ROWS _Pragma("omp parallel for schedule(static)")
 
 enum { ORC_SSBICGSAFE2 = 0, ORC_P_BICGSAFE = 1, ORC_P_BICGSAFE_RR = 2 };
 enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_ERR_ARG = -1, ORC_ERR_BREAKDOWN = -3, ORC_ERR_NONFINITE = -5 };
@@ -81,6 +94,7 @@ typedef struct {
 void orc_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
               const double* x, double* y)
 {
+    ORC_ROWS
     for (int64_t i = 0; i < n; ++i) {
         double acc = 0.0;
         for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) acc = fma(val[k], x[col[k]], acc);
@@ -156,16 +170,12 @@ static double big_round(const bigfix* a0)
     return neg ? -r : r;
 }
 
-double orc_dot(int64_t n, const double* x, const double* y)
+/* Adds x_i y_i for i in [i0, i1) exactly into a; returns 0 (and stops) at a
+ * non-finite operand. */
+static int dot_accumulate(bigfix* a, int64_t i0, int64_t i1, const double* x, const double* y)
 {
-    bigfix a;
-    memset(&a, 0, sizeof(a));
-    for (int64_t i = 0; i < n; ++i) {
-        if (!isfinite(x[i]) || !isfinite(y[i])) {
-            double s = 0.0;
-            for (int64_t j = 0; j < n; ++j) s += x[j] * y[j];
-            return s;
-        }
+    for (int64_t i = i0; i < i1; ++i) {
+        if (!isfinite(x[i]) || !isfinite(y[i])) return 0;
         uint64_t mx, my;
         int ex, ey;
         split(x[i], &mx, &ex);
@@ -179,9 +189,56 @@ double orc_dot(int64_t n, const double* x, const double* y)
         uint64_t v0 = lo << sh;
         uint64_t v1 = sh ? ((lo >> (64 - sh)) | (hi << sh)) : hi;
         uint64_t v2 = sh ? (hi >> (64 - sh)) : 0;
-        big_addsub(&a, limb, v0, neg);
-        big_addsub(&a, limb + 1, v1, neg);
-        big_addsub(&a, limb + 2, v2, neg);
+        big_addsub(a, limb, v0, neg);
+        big_addsub(a, limb + 1, v1, neg);
+        big_addsub(a, limb + 2, v2, neg);
+    }
+    return 1;
+}
+
+/* a += b exactly (two's complement integers of XB_LIMBS limbs). */
+static void big_add(bigfix* a, const bigfix* b)
+{
+    uint64_t carry = 0;
+    for (int k = 0; k < XB_LIMBS; ++k) {
+        uint64_t o = a->l[k];
+        uint64_t s1 = o + b->l[k];
+        uint64_t c1 = s1 < o;
+        uint64_t s2 = s1 + carry;
+        uint64_t c2 = s2 < s1;
+        a->l[k] = s2;
+        carry = c1 | c2;
+    }
+}
+
+double orc_dot(int64_t n, const double* x, const double* y)
+{
+    bigfix a;
+    memset(&a, 0, sizeof(a));
+    int finite_ops = 1;
+#ifdef _OPENMP
+    #pragma omp parallel
+    {
+        bigfix part;
+        memset(&part, 0, sizeof(part));
+        const int64_t nt = omp_get_num_threads(), t = omp_get_thread_num();
+        const int64_t i0 = n * t / nt, i1 = n * (t + 1) / nt;
+        const int ok = dot_accumulate(&part, i0, i1, x, y);
+        #pragma omp critical
+        {
+            big_add(&a, &part);
+            if (!ok) finite_ops = 0;
+        }
+    }
+#else
+    finite_ops = dot_accumulate(&a, 0, n, x, y);
+#endif
+    if (!finite_ops) {
+        /* a NaN or infinity among the operands: the plain left-to-right sum,
+           so that it propagates as IEEE arithmetic does */
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) s += x[j] * y[j];
+        return s;
     }
     return big_round(&a);
 }
@@ -191,8 +248,10 @@ double orc_true_residual(int64_t n, const int64_t* rowptr, const int32_t* col, c
                          const double* b, const double* x)
 {
     double* ax = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    ORC_ROWS
     for (int64_t i = 0; i < n; ++i) ax[i] = 0.0;
     orc_spmv(n, rowptr, col, val, x, ax);
+    ORC_ROWS
     for (int64_t i = 0; i < n; ++i) ax[i] = b[i] - ax[i];
     double r = sqrt(orc_dot(n, ax, ax));
     free(ax);
@@ -229,7 +288,9 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
 
     /* Alg. 3/4/5 set-up: r_0 = b - A x_0, r0* = r_0 (R8). */
     orc_spmv(n, w->rowptr, w->col, w->val, x, As);            /* A x_0 (As used as scratch) */
+    ORC_ROWS
     for (int64_t j = 0; j < n; ++j) r[j] = w->b[j] - As[j];
+    ORC_ROWS
     for (int64_t j = 0; j < n; ++j) rs[j] = r[j];
     /* R2: zero auxiliaries. */
     for (int k = SV_Y; k < SV_COUNT; ++k)
@@ -303,10 +364,13 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
         if (i >= it_budget) { *its = i; return ORC_NOT_CONVERGED; }
 
         /* p_i = r_i + beta_i (p_{i-1} - u_{i-1}) */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) p[j] = fma(beta, p[j] - u[j], r[j]);
         /* o_i = s_i + beta_i t_{i-1} */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) ov[j] = fma(beta, t[j], s[j]);
         /* u_i = zeta_i o_i + eta_i (y_i + beta_i u_{i-1}) */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) u[j] = fma(zeta, ov[j], eta * fma(beta, u[j], y[j]));
         if (!pipelined) {
             /* Alg. 3: w_i = A u_i */
@@ -317,21 +381,28 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
             orc_spmv(n, w->rowptr, w->col, w->val, u, wv);
         } else {
             /* q_i = As_i + beta_i l_{i-1}   (Eq. q) */
+            ORC_ROWS
             for (int64_t j = 0; j < n; ++j) q[j] = fma(beta, l[j], As[j]);
             /* w_i = zeta_i q_i + eta_i (g_i + beta_i w_{i-1})   (Eq. w) */
+            ORC_ROWS
             for (int64_t j = 0; j < n; ++j) wv[j] = fma(zeta, q[j], eta * fma(beta, wv[j], g[j]));
         }
         /* t_i = o_i - w_i */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) t[j] = ov[j] - wv[j];
         /* z_i = zeta_i r_i + eta_i z_{i-1} - alpha_i u_i */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) z[j] = fma(-alpha, u[j], fma(zeta, r[j], eta * z[j]));
         /* y_{i+1} = zeta_i s_i + eta_i y_i - alpha_i w_i */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) y[j] = fma(-alpha, wv[j], fma(zeta, s[j], eta * y[j]));
         /* x_{i+1} = x_i + alpha_i p_i + z_i */
+        ORC_ROWS
         for (int64_t j = 0; j < n; ++j) x[j] = fma(alpha, p[j], x[j]) + z[j];
         if (rr_step) {
             /* Alg. 5 replacement: r = b - A x, l_i = A t_i (R9), g = A y, s = A r */
             orc_spmv(n, w->rowptr, w->col, w->val, x, Aw);
+            ORC_ROWS
             for (int64_t j = 0; j < n; ++j) r[j] = w->b[j] - Aw[j];
             orc_spmv(n, w->rowptr, w->col, w->val, t, l);
             orc_spmv(n, w->rowptr, w->col, w->val, y, g);
@@ -339,13 +410,17 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
             res->rr_steps++;
         } else {
             /* r_{i+1} = r_i - alpha_i o_i - y_{i+1} */
+            ORC_ROWS
             for (int64_t j = 0; j < n; ++j) r[j] = fma(-alpha, ov[j], r[j]) - y[j];
             if (pipelined) {
                 /* Aw_i; l_i = q_i - Aw_i (Eq. l); g_{i+1} = zeta As_i + eta g_i - alpha Aw_i (Eq. g);
                    s_{i+1} = s_i - alpha q_i - g_{i+1} (Eq. sip1) */
                 orc_spmv(n, w->rowptr, w->col, w->val, wv, Aw);
+                ORC_ROWS
                 for (int64_t j = 0; j < n; ++j) l[j] = q[j] - Aw[j];
+                ORC_ROWS
                 for (int64_t j = 0; j < n; ++j) g[j] = fma(-alpha, Aw[j], fma(zeta, As[j], eta * g[j]));
+                ORC_ROWS
                 for (int64_t j = 0; j < n; ++j) s[j] = fma(-alpha, q[j], s[j]) - g[j];
             }
         }

@@ -10,18 +10,24 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "bicgsafe_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+# The same source built with OpenMP: row loops and inner products over all
+# host cores, bit-identical results.  Used only to time the CPU baseline on
+# every core; the parity oracle is the single-threaded LIB.
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
 
-def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, SRC, "-lm"]
+def build(force: bool = False, parallel: bool = False) -> str:
+    lib = LIB_OMP if parallel else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC):
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + \
+        (["-fopenmp"] if parallel else []) + ["-o", tmp, SRC, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force=True))
+    print(build(force=True, parallel=True))

@@ -5,10 +5,20 @@ are (a) the first 20 iterations, which the oracle can run, and (b) properties
 that hold at any size, measured by the oracle on the GPU's output: the FP64
 true residual ||b - A x|| / ||b|| <= 1e-10 at exit.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cd3d128_full_solves.json")
+
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<f8").tobytes()).hexdigest()
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +60,37 @@ def test_cd3d_128_first_20_iterations(env, cd3d, kind):
     assert np.array_equal(h[:n], ref["hist"][:n])
     assert np.array_equal(sc[:20], ref["scalars"][:20])
     assert np.array_equal(x.cpu().numpy(), ref["x"])
+
+
+@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe", "p-BiCGSafe-rr"])
+def test_cd3d_128_full_solve_matches_oracle(env, cd3d, kind):
+    """The complete FP64 solve of the benchmark system, in the benchmark's launch configuration
+    and options, against the oracle's complete solve (tests/golden/cd3d128_full_solves.json,
+    written by make_cd3d128_full_solves.py from oracle/ alone): the iteration count within 5 %
+    of the oracle's -- and in fact the same iterations, outer runs and replacement steps, and
+    the same x, bit for bit."""
+    bcs, torch, orc = env
+    A, b, M = cd3d
+    with open(GOLDEN) as fh:
+        gold = json.load(fh)
+    assert _sha(b) == gold["b_sha256"], "the input generator gives a different b than the golden run"
+    o = gold["options"]
+    g = gold["solves"][kind]
+    S = bcs.solver_create(M, kind, tol=o["tol"], maxit=o["maxit"], max_outer=o["max_runs"], rr_m=o["rr_m"],
+                          rr_M=o["rr_M"])
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    assert g["status"] == "ok" and res["status"] == bcs.OK
+    assert abs(res["iterations"] - g["iterations"]) <= 0.05 * g["iterations"]
+    assert res["iterations"] == g["iterations"]
+    assert res["outer_steps"] == g["outer_steps"]
+    assert res["rr_steps"] == g["rr_steps"]
+    xh = x.cpu().numpy()
+    rows = np.asarray(gold["sample_rows"])
+    assert np.array_equal(xh[rows], np.array([float.fromhex(v) for v in g["x_sample"]]))
+    assert _sha(xh) == g["x_sha256"]
+    assert res["rel_res_true"] == float.fromhex(g["rel_res_true"])
 
 
 @pytest.mark.parametrize("kind,prec", [("ssBiCGSafe2", "fp64"), ("p-BiCGSafe", "fp64"), ("p-BiCGSafe", "fp32"),

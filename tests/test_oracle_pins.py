@@ -396,3 +396,29 @@ def test_bf16_round_to_nearest_even(orc):
     f = rng.standard_normal(1000).astype(np.float32)
     tb = torch.from_numpy(f).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
     assert np.array_equal(orc.to_bf16_bits(f.astype(np.float64)), tb)
+
+
+def test_all_cores_build_is_bit_identical(orc):
+    """The OpenMP build of the same source (the all-cores CPU baseline) gives the single-threaded
+    oracle's bits: SpMV rows, the vector recurrences and the correctly rounded inner products
+    (exact per-thread partial sums merged exactly; checked on sums that cancel heavily and on a
+    non-finite operand), and whole solves of all three methods with a restart."""
+    rng = np.random.default_rng(11)
+    n = 100003
+    x = rng.standard_normal(n) * 10.0 ** rng.integers(-30, 30, n)
+    y = rng.standard_normal(n)
+    for a, b in [(x, y), (x, -x[::-1].copy()), (np.concatenate([x, -x]), np.concatenate([y, y]))]:
+        assert orc.dot(a, b, parallel=True) == orc.dot(a, b)
+    bad = y.copy()
+    bad[n // 2] = np.inf
+    assert np.isnan(orc.dot(x * 0, bad, parallel=True)) == np.isnan(orc.dot(x * 0, bad))
+    A = W.cd2d(24, 20.0)
+    b = W.rhs_ones(A)
+    xs = rng.standard_normal(A.n)
+    assert np.array_equal(orc.spmv(A, xs, parallel=True), orc.spmv(A, xs))
+    for kind in ["ssBiCGSafe2", "p-BiCGSafe", "p-BiCGSafe-rr"]:
+        r1 = orc.solve(A, b, kind=kind, tol=1e-12, maxit=400, rr_m=25, max_restarts=3)
+        r8 = orc.solve(A, b, kind=kind, tol=1e-12, maxit=400, rr_m=25, max_restarts=3, parallel=True)
+        assert r1["iterations"] == r8["iterations"] and r1["restarts"] == r8["restarts"]
+        assert np.array_equal(r1["hist"], r8["hist"])
+        assert np.array_equal(r1["x"], r8["x"])
