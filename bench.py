@@ -30,9 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-10 rel. residual, pipelined vs plain; HBM GB/s per iter; solves/s"
 HBM_PEAK_FALLBACK = 6800.0
-SMS = 152
-DFMA_PER_CLK_SM = 2          # GB300: FP64 FMA issue rate per SM per clock
-SM_MAX_MHZ = 2070.0
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal; the FP64 units also bound the FP64 kernel)
+GOLDEN = os.path.join(ROOT, "tests", "golden", "cd3d128_full_solves.json")
 
 
 # DRAM traffic of the solve kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on this
@@ -144,6 +143,37 @@ def make_workload(k=128):
     return A, b
 
 
+def oracle_golden():
+    """The oracle's complete FP64 solves of the 128^3 system (iterations, outer runs, x digest and
+    x at sampled rows), written by tests/golden/make_cd3d128_full_solves.py from oracle/ alone."""
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def x_sha256(x):
+    return hashlib.sha256(np.ascontiguousarray(x, dtype="<f8").tobytes()).hexdigest()
+
+
+def error_vs_oracle(x, kind, gold):
+    """Error of a returned x against the FP64 oracle's x for the same method: max |x - x_oracle|
+    over the golden file's 4096 sampled rows, and whether the whole vector is bit-identical."""
+    g = gold["solves"].get(kind)
+    if g is None:
+        return None
+    rows = np.asarray(gold["sample_rows"])
+    ref = np.array([float.fromhex(v) for v in g["x_sample"]])
+    return {"oracle_kind": kind, "max_abs_err_sampled": float(np.max(np.abs(x[rows] - ref))),
+            "sampled_rows": len(rows), "bit_identical": x_sha256(x) == g["x_sha256"],
+            "oracle_iterations": g["iterations"], "oracle_outer_steps": g["outer_steps"]}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 # ---- algorithmic work per solve ---------------------------------------------------------
 
 def flops_per_iter(kind, n, nnz):
@@ -228,38 +258,55 @@ class Clocks:
 
 # ---- the CPU oracle baseline ---------------------------------------------------------------
 
-def cpu_sample(A, b, kind, iters):
-    """Time `iters` iterations of the CPU oracle (single thread) on the full system."""
+def cpu_sample(A, b, kind, iters, parallel=False):
+    """Time `iters` iterations of the CPU oracle on the full system: the single-threaded parity
+    build, or (parallel) the same source built with OpenMP on every host core."""
     import oracle
-    oracle.lib()
+    oracle.lib(parallel)
     t0 = time.perf_counter()
-    o = oracle.solve(A, b, kind=kind, tol=0.0, maxit=iters)
+    o = oracle.solve(A, b, kind=kind, tol=0.0, maxit=iters, parallel=parallel)
     dt = time.perf_counter() - t0
     return dt, o
 
 
 def reference_arm(a):
+    """The oracle (all host cores) on the benchmark's workload: each step times a bounded sample of
+    iterations, scaled to one solve by the oracle's own iteration count for that method (the
+    golden file of its complete solves)."""
     A, b = make_workload(a.size)
     kind = a.kind
-    # iterations of one full solve of this system to 1e-10 (the oracle's count with the true-residual
-    # restarts; the FP64 GPU solve reproduces it exactly)
-    iters_full = {"p-BiCGSafe": 428, "ssBiCGSafe2": 370, "p-BiCGSafe-rr": 407}.get(kind, 428)
-    per = max(2, min(a.cpu_iters, 20))
+    gold = oracle_golden()
+    cores = host_cores()
     times = []
-    for s in range(a.warmup + a.steps):
-        dt, _ = cpu_sample(A, b, kind, per)
-        if s >= a.warmup:
-            times.append(dt)
-    sec_per_iter = sum(times) / (len(times) * per)
-    solve_s = sec_per_iter * iters_full
+    if a.size == 128 and kind in gold["solves"]:
+        iters_full = gold["solves"][kind]["iterations"]
+        per = max(2, min(a.cpu_iters, 20))
+        for s in range(a.warmup + a.steps):
+            dt, _ = cpu_sample(A, b, kind, per, parallel=True)
+            if s >= a.warmup:
+                times.append(dt)
+        solve_s = sum(times) / (len(times) * per) * iters_full
+        sample = ("each step: %d iterations of the FP64 oracle (OpenMP build of the same source, bit-identical, "
+                  "%d threads) on the full system, scaled to one solve by the oracle's complete-solve count of "
+                  "%d iterations" % (per, cores, iters_full))
+    else:
+        # a system outside the golden file: every step is one complete oracle solve (small grids only)
+        import oracle
+        oracle.lib(True)
+        for s in range(a.warmup + a.steps):
+            t0 = time.perf_counter()
+            oracle.solve(A, b, kind=kind, tol=1e-10, maxit=a.maxit, max_restarts=29, parallel=True)
+            if s >= a.warmup:
+                times.append(time.perf_counter() - t0)
+        solve_s = sum(times) / len(times)
+        sample = ("each step: one complete solve to 1e-10 by the FP64 oracle (OpenMP build of the same source, "
+                  "%d threads)" % cores)
     val = 1.0 / solve_s
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(a, A.n, A.nnz),
-            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: %d iterations of the single-threaded FP64 oracle on the full "
-                                       "system, scaled to one solve by %d iterations" % (per, iters_full)},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -390,6 +437,7 @@ def main():
 
     A, b = make_workload(a.size)
     n, nnz = A.n, A.nnz
+    gold = oracle_golden() if a.size == 128 else None
     layouts = bcs.LAYOUT_CSR | (bcs.LAYOUT_SELL if a.layout == "sell" else 0)
     M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32 | bcs.STORE_BF16)
     stream = torch.cuda.current_stream()
@@ -429,8 +477,11 @@ def main():
             dist.barrier()
         total_ms = t0.elapsed_time(t1)
         per = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]
-        # accuracy of the last solve against the exact solution of A x = A 1 (outside the timed region)
+        # accuracy of the last solve against the exact solution of A x = A 1 and against the FP64
+        # oracle's x for the same method (outside the timed region)
         results[-1]["max_abs_err_vs_ones"] = float((xd - 1.0).abs().max().item())
+        if gold is not None:
+            results[-1]["error_vs_oracle"] = error_vs_oracle(xd.cpu().numpy(), kind, gold)
         return total_ms, per, results
 
     if a.profile:
@@ -454,12 +505,13 @@ def main():
     iters, outer = r0["iterations"], r0["outer_steps"]
     kernel_ms = statistics.mean(per)
 
-    # roofline of the solve kernel (the only kernel in the step)
+    # roofline of the solve kernel (the only kernel in the step): HBM, on the algorithmic bytes of
+    # the solve (two matrix passes and V + 2 vector passes per iteration, plus each outer step's
+    # set-up), against the measured copy bandwidth; the FP64 units' share beside it
     peaks, peak_src = measured_peaks()
     lo = a.precision != "fp64"
     vb, mb = (4, 4 if a.precision == "fp32" else 2) if lo else (8, 8)
     f, by = solve_work(a.kind, n, nnz, iters, outer, vb, mb)
-    fp64_peak = SMS * DFMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6
     achieved_tf = f / (kernel_ms * 1e-3) / 1e12
     achieved_gbs = by / (kernel_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
@@ -471,16 +523,16 @@ def main():
     kname = "solve_kernel<%s,%s,%s,1,static>" % ("float" if lo else "double",
                                         {"fp64": "double", "fp32": "float", "bf16": "bf16"}[a.precision],
                                         a.layout.upper())
-    hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-           "peak_source": peak_src}
-    if lo:
-        # FP32/BF16 vectors: the FP64 units only accumulate the inner products; HBM bounds the kernel
-        roofline = dict(bound="hbm", traffic=traffic, kernel=kname, **hbm)
-    else:
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved_tf / (fp64_peak / 1e12), "traffic": traffic,
-                    "kernel": kname, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 "
-                    "flop x 2070 MHz (FP64 ALU; the kernel's binding unit on GB300)", "hbm": hbm}
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic, "kernel": kname,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src if peak_src == "measured"
+                else "fallback 6800 GB/s",
+                "algorithmic_bytes": by, "traffic_vs_algorithmic": None if traffic is None else traffic / by}
+    if not lo:
+        roofline["fp64_units"] = {"achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
+                                  "peak_source": "nominal GB300 FP64 rate (Table 1 flops: 2 SpMVs + 48 "
+                                                 "vector flops per row per iteration)"}
 
     # end to end through the public API with host buffers
     bh = torch.from_numpy(b).pin_memory().numpy()
@@ -507,21 +559,33 @@ def main():
                            ("p-BiCGSafe-rr", "fp64")]:
             tm, pr, rs = run(kind, prec, 3, 1)
             rr = rs[-1]
-            extras["%s_%s" % (kind, prec)] = {
-                "ms_per_solve": tm / 3, "iterations": rr["iterations"], "outer_steps": rr["outer_steps"],
-                "rel_res_true": rr["rel_res_true"], "max_abs_err_vs_ones": rr["max_abs_err_vs_ones"],
-                "status": rr["status_name"],
-                "us_per_iter": 1e3 * tm / 3 / max(1, rr["iterations"])}
+            e = {"ms_per_solve": tm / 3, "iterations": rr["iterations"], "outer_steps": rr["outer_steps"],
+                 "rel_res_true": rr["rel_res_true"], "max_abs_err_vs_ones": rr["max_abs_err_vs_ones"],
+                 "error_vs_oracle": rr.get("error_vs_oracle"), "status": rr["status_name"],
+                 "us_per_iter": 1e3 * tm / 3 / max(1, rr["iterations"])}
+            pvb, pmb = (8, 8) if prec == "fp64" else (4, 4 if prec == "fp32" else 2)
+            _, pby = solve_work(kind, n, nnz, rr["iterations"], rr["outer_steps"], pvb, pmb)
+            pgbs = pby / (statistics.mean(pr) * 1e-3) / 1e9
+            e["hbm"] = {"achieved": pgbs, "peak": hbm_peak, "unit": "GB/s", "frac": pgbs / hbm_peak}
+            extras["%s_%s" % (kind, prec)] = e
 
     line = None
     if rank == 0:
         cpu = None
         if world == 1:
-            dt, o = cpu_sample(A, b, a.kind, a.cpu_iters)
-            solve_s = dt / a.cpu_iters * iters
-            cpu = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                   "sample": "%d iterations of the single-threaded FP64 oracle (%s) on the full system in %.1f s, "
-                             "scaled to one solve by the GPU solve's %d iterations" % (a.cpu_iters, a.kind, dt, iters)}
+            # the oracle's own complete-solve iteration count scales the samples (the GPU's when the
+            # golden file does not cover this configuration)
+            g_it = gold["solves"][a.kind]["iterations"] if gold and a.kind in gold["solves"] else iters
+            cores = host_cores()
+            dtp, _ = cpu_sample(A, b, a.kind, a.cpu_iters, parallel=True)
+            dt1, _ = cpu_sample(A, b, a.kind, a.cpu_iters)
+            cpu = {"value": a.cpu_iters / (dtp * g_it), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": "%d iterations of the FP64 oracle (%s; OpenMP build of the same source, bit-identical, "
+                             "%d threads) on the full system in %.2f s, scaled to one solve by the oracle's %d "
+                             "iterations" % (a.cpu_iters, a.kind, cores, dtp, g_it),
+                   "single_thread": {"value": a.cpu_iters / (dt1 * g_it), "unit": "solves/s", "cores": 1,
+                                     "sample": "the same %d iterations with the single-threaded parity build in "
+                                               "%.1f s" % (a.cpu_iters, dt1)}}
         line = {"metric": METRIC, "value": world * 1e3 / ms_per_step, "unit": "solves/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
@@ -529,6 +593,7 @@ def main():
                 "config": bench_config(a, n, nnz, world),
                 "iterations": iters, "outer_steps": outer, "converged_all_steps": ok,
                 "rel_res_true": r0["rel_res_true"], "max_abs_err_vs_ones": r0["max_abs_err_vs_ones"],
+                "error_vs_oracle": r0.get("error_vs_oracle"),
                 "kernel_ms": kernel_ms,
                 "us_per_iter": 1e3 * kernel_ms / max(1, iters),
                 "gb_per_s_per_iter": achieved_gbs,

@@ -203,16 +203,23 @@ int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result
  * entry point exists for callers that cannot allocate device memory -- code
  * whose device memory is all owned by another allocator (for example a
  * framework's caching allocator), or latency-sensitive loops in which a
- * cudaMalloc/cudaFree (which synchronise the device) would stall.  It computes
- * the same correctly rounded (x, y) as bcs_dot with the same kernels, but the
- * per-CTA partial sums go to a fixed 128 KiB array that the library holds on
- * every GPU that loads it until the process exits (at most 256 CTAs).
+ * cudaMalloc/cudaFree (which synchronise the device) would stall.  It runs
+ * bcs_dot's kernels, but the per-CTA partial sums go to a fixed 128 KiB array
+ * that the library holds on every GPU that loads it until the process exits
+ * (at most 256 CTAs).  The value is the correctly rounded (x, y), as bcs_dot's
+ * is, unless the sum cancels by more than about 2^50 relative to its largest
+ * product: each lane's window drops bits more than 2^-108 below its largest
+ * term, and the two calls give the terms to different numbers of CTAs, so
+ * under such cancellation their last bits may differ.
  *   n           number of elements, 0 <= n <= 2^33 (BCS_ERR_ARG beyond that).
  *   x, y        device vectors, FP64 when vec_f32 == 0, FP32 otherwise.
  *   result_dev  device double receiving the value; written asynchronously on
  *               stream (synchronise before reading it).
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current) and keeps it for the process; make that first call before
+ * any stream capture.  cudaDeviceReset unloads the library's device code, so
+ * the kept address is no longer valid: do not call this entry point on a
+ * device after resetting it in the same process.  All calls
  * share the one array, so calls that overlap on the GPU (different streams,
  * or different host threads on one device) race: serialise them.  Calls no
  * cudaMalloc, cudaFree or other allocating routine.

@@ -153,9 +153,18 @@ def _np(a, dtype):
 
 
 def _stream(stream):
-    if stream is None:
-        return None
-    return stream if isinstance(stream, int) else stream.cuda_stream
+    """The CUDA stream handle to pass: an explicit stream (torch stream or raw handle), else torch's
+    current stream, so that a call made inside `with torch.cuda.stream(s)` is ordered after the work
+    already queued on s (torch creates its side streams non-blocking: the legacy default stream does
+    not wait for them).  NULL when torch has not initialised CUDA (its current stream is then the
+    default stream)."""
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+        return torch.cuda.current_stream().cuda_stream or None
+    return None
 
 
 def _precision(p):

@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
 
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        [os.path.join(INCLUDE, "bcs.h")]
+        glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
 def _compile(src, obj, verbose):
