@@ -44,6 +44,9 @@ class _Result(ctypes.Structure):
 
 
 _LIBS = {}
+_DP = ctypes.POINTER(ctypes.c_double)
+_MV_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, _DP, _DP)
+_DOT_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, _DP, _DP)
 
 
 def lib(parallel=False):
@@ -67,6 +70,17 @@ def lib(parallel=False):
         L.orc_sell_build.restype = ctypes.c_int64
         L.orc_to_bf16.argtypes = [ctypes.c_int64, P, P]
         L.orc_to_bf16.restype = None
+        L.orc_dot_limbs.argtypes = []
+        L.orc_dot_limbs.restype = ctypes.c_int
+        L.orc_dot_partial.argtypes = [ctypes.c_int64, P, P, P]
+        L.orc_dot_partial.restype = ctypes.c_int
+        L.orc_dot_merge.argtypes = [P, P]
+        L.orc_dot_merge.restype = None
+        L.orc_dot_round.argtypes = [P]
+        L.orc_dot_round.restype = ctypes.c_double
+        L.orc_solve_hooked.argtypes = [ctypes.c_int64, P, P, ctypes.POINTER(_Opts), _MV_FN, _DOT_FN, P, P,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(_Result)]
+        L.orc_solve_hooked.restype = ctypes.c_int
         _LIBS[parallel] = L
     return _LIBS[parallel]
 
@@ -160,3 +174,71 @@ def to_bf16_bits(v):
     out = np.zeros(len(v), dtype=np.uint16)
     lib().orc_to_bf16(len(v), _p(v), _p(out))
     return out
+
+
+# ---- a row-partitioned run (orc_solve_hooked) --------------------------------------------------
+
+def dot_partial(x, y):
+    """Exact partial sum of x_i y_i as integer limbs (uint64 array) and whether every operand was
+    finite; partials of disjoint row blocks merge exactly (dot_merge) and round once (dot_round)."""
+    L = lib()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    limbs = np.zeros(L.orc_dot_limbs(), dtype=np.uint64)
+    ok = L.orc_dot_partial(len(x), _p(x), _p(y), _p(limbs))
+    return limbs, bool(ok)
+
+
+def dot_merge(partials):
+    """Exact sum of partials (in the given order; the sum is exact, so any order gives it)."""
+    L = lib()
+    acc = np.zeros(L.orc_dot_limbs(), dtype=np.uint64)
+    for p in partials:
+        p = np.ascontiguousarray(p, dtype=np.uint64)
+        L.orc_dot_merge(_p(acc), _p(p))
+    return acc
+
+
+def dot_round(limbs):
+    limbs = np.ascontiguousarray(limbs, dtype=np.uint64)
+    return lib().orc_dot_round(_p(limbs))
+
+
+def solve_hooked(n_local, b, mv, dot, x0=None, kind="p-BiCGSafe", tol=1e-10, maxit=10000, rr_m=100, rr_M=None,
+                 max_restarts=0, hist_cap=None):
+    """Algorithms 3/4/5 over one block of rows of a partitioned system: mv(x, y) sets y = A x on
+    the block's rows and dot(x, y) returns the inner product over all rows (numpy views of the
+    block's parts).  Returns the same dict as solve() without the state dump."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n_local) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    errors = []
+
+    def _mv(ctx, xp, yp):
+        try:
+            mv(np.ctypeslib.as_array(xp, (n_local,)), np.ctypeslib.as_array(yp, (n_local,)))
+        except Exception as e:  # noqa: BLE001  (reported after the run)
+            errors.append(e)
+
+    def _dot(ctx, xp, yp):
+        try:
+            return float(dot(np.ctypeslib.as_array(xp, (n_local,)), np.ctypeslib.as_array(yp, (n_local,))))
+        except Exception as e:  # noqa: BLE001
+            errors.append(e)
+            return float("nan")
+
+    mvf, dotf = _MV_FN(_mv), _DOT_FN(_dot)
+    o = _Opts(KINDS[kind] if isinstance(kind, str) else int(kind), tol, maxit, rr_m,
+              maxit + 1 if rr_M is None else rr_M, max_restarts, -1, 0)
+    cap = (maxit + 1) * (max_restarts + 1) + 4 if hist_cap is None else hist_cap
+    hist = np.zeros(cap)
+    scal = np.zeros(4 * cap)
+    hl = ctypes.c_int(0)
+    res = _Result()
+    st = lib().orc_solve_hooked(n_local, _p(b), _p(x), ctypes.byref(o), mvf, dotf, None, _p(hist), cap,
+                                ctypes.byref(hl), _p(scal), ctypes.byref(res))
+    if errors:
+        raise errors[0]
+    k = min(res.iterations + 1, cap)
+    return dict(x=x, hist=hist[:hl.value].copy(), status=st, status_name=STATUS.get(st, str(st)),
+                iterations=res.iterations, restarts=res.restarts, rr_steps=res.rr_steps,
+                rel_res_true=res.rel_res_true, scalars=scal[:4 * k].reshape(-1, 4).copy())

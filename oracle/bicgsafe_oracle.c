@@ -243,6 +243,37 @@ double orc_dot(int64_t n, const double* x, const double* y)
     return big_round(&a);
 }
 
+/*
+ * The pieces of orc_dot for a sum split over several owners of the rows (a
+ * row-partitioned run): the exact partial sum of x_i y_i over [0, n) as
+ * XB_LIMBS 64-bit limbs (two's complement fixed point, bit XB_BIAS = 2^0;
+ * returns 0 when an operand is not finite), the exact merge of two partials,
+ * and the final rounding to nearest even.
+ */
+int orc_dot_limbs(void) { return XB_LIMBS; }
+int orc_dot_partial(int64_t n, const double* x, const double* y, uint64_t* limbs)
+{
+    bigfix a;
+    memset(&a, 0, sizeof(a));
+    const int ok = dot_accumulate(&a, 0, n, x, y);
+    memcpy(limbs, a.l, sizeof(a.l));
+    return ok;
+}
+void orc_dot_merge(uint64_t* a, const uint64_t* b)
+{
+    bigfix x, y;
+    memcpy(x.l, a, sizeof(x.l));
+    memcpy(y.l, b, sizeof(y.l));
+    big_add(&x, &y);
+    memcpy(a, x.l, sizeof(x.l));
+}
+double orc_dot_round(const uint64_t* limbs)
+{
+    bigfix a;
+    memcpy(a.l, limbs, sizeof(a.l));
+    return big_round(&a);
+}
+
 /* ||b - A x||_2, computed with the routines above. */
 double orc_true_residual(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
                          const double* b, const double* x)
@@ -262,12 +293,52 @@ static int finite(double v) { return isfinite(v); }
 
 /* ---- one run of Algorithm 3 / 4 / 5 ----------------------------------- */
 
+/*
+ * The two operations of the method that involve every row: y = A x and the
+ * inner product (x, y).  A plain run uses the CSR routines above on the whole
+ * system; a row-partitioned run (orc_solve_hooked) supplies its own, over its
+ * block of rows, with the halo exchange and the sum over all blocks inside.
+ */
+typedef void (*orc_mv_fn)(void* ctx, const double* x, double* y);
+typedef double (*orc_dot_fn)(void* ctx, const double* x, const double* y);
+
 typedef struct {
     int64_t n;
     const int64_t* rowptr; const int32_t* col; const double* val;
     const double* b;
     double* v[SV_COUNT];
+    orc_mv_fn mv;
+    orc_dot_fn dot;
+    void* ctx;
 } orc_ws;
+
+#define MV(x, y) w->mv(w->ctx, (x), (y))
+#define DOT(x, y) w->dot(w->ctx, (x), (y))
+
+static void mv_whole(void* ctx, const double* x, double* y)
+{
+    const orc_ws* w = (const orc_ws*)ctx;
+    orc_spmv(w->n, w->rowptr, w->col, w->val, x, y);
+}
+static double dot_whole(void* ctx, const double* x, const double* y)
+{
+    return orc_dot(((const orc_ws*)ctx)->n, x, y);
+}
+
+/* ||b - A x||_2 with the run's operations (the same steps as orc_true_residual). */
+static double ws_true_residual(orc_ws* w, const double* x)
+{
+    const int64_t n = w->n;
+    double* ax = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    ORC_ROWS
+    for (int64_t i = 0; i < n; ++i) ax[i] = 0.0;
+    MV(x, ax);
+    ORC_ROWS
+    for (int64_t i = 0; i < n; ++i) ax[i] = w->b[i] - ax[i];
+    double r = sqrt(DOT(ax, ax));
+    free(ax);
+    return r;
+}
 
 /*
  * One run from the current x.  thresh = absolute threshold of the stop test
@@ -287,7 +358,7 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
     const int rr = (o->kind == ORC_P_BICGSAFE_RR);
 
     /* Alg. 3/4/5 set-up: r_0 = b - A x_0, r0* = r_0 (R8). */
-    orc_spmv(n, w->rowptr, w->col, w->val, x, As);            /* A x_0 (As used as scratch) */
+    MV(x, As);                                                /* A x_0 (As used as scratch) */
     ORC_ROWS
     for (int64_t j = 0; j < n; ++j) r[j] = w->b[j] - As[j];
     ORC_ROWS
@@ -297,21 +368,21 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
         if (k != SV_S) memset(w->v[k], 0, sizeof(double) * (size_t)n);
     memset(s, 0, sizeof(double) * (size_t)n);
     /* R1: s_0 = A r_0 for the pipelined variants. */
-    if (pipelined) orc_spmv(n, w->rowptr, w->col, w->val, r, s);
+    if (pipelined) MV(r, s);
 
     double alpha_prev = 0.0, zeta_prev = 0.0, f_prev = 0.0;
     for (int i = 0;; ++i) {
         double alpha, beta, zeta, eta;
         double da, db = 0, dc = 0, dd, de = 0, df, dg, dh = 0, drr;
         /* Alg. 3: s_i = A r_i.   Alg. 4/5: As_i = A s_i. */
-        if (pipelined) orc_spmv(n, w->rowptr, w->col, w->val, s, As);
-        else           orc_spmv(n, w->rowptr, w->col, w->val, r, s);
+        if (pipelined) MV(s, As);
+        else           MV(r, s);
         /* Inner products (R5). */
-        da = orc_dot(n, s, s);
-        dd = orc_dot(n, s, r);
-        df = orc_dot(n, rs, r);
-        dg = orc_dot(n, rs, s);
-        drr = orc_dot(n, r, r);
+        da = DOT(s, s);
+        dd = DOT(s, r);
+        df = DOT(rs, r);
+        dg = DOT(rs, s);
+        drr = DOT(r, r);
         if (i == 0) {
             /* R3: the i = 0 branch. */
             beta = 0.0;
@@ -322,10 +393,10 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
                 if (!(sqrt(drr) <= thresh)) return ORC_ERR_BREAKDOWN;
             }
         } else {
-            db = orc_dot(n, y, y);
-            dc = orc_dot(n, s, y);
-            de = orc_dot(n, y, r);
-            dh = orc_dot(n, rs, t);
+            db = DOT(y, y);
+            dc = DOT(s, y);
+            de = DOT(y, r);
+            dh = DOT(rs, t);
             beta = (alpha_prev * df) / (zeta_prev * f_prev);
             alpha = df / (dg + beta * dh);
             double den = da * db - dc * dc;
@@ -374,11 +445,11 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
         for (int64_t j = 0; j < n; ++j) u[j] = fma(zeta, ov[j], eta * fma(beta, u[j], y[j]));
         if (!pipelined) {
             /* Alg. 3: w_i = A u_i */
-            orc_spmv(n, w->rowptr, w->col, w->val, u, wv);
+            MV(u, wv);
         } else if (rr_step) {
             /* Alg. 5: q_i = A o_i, w_i = A u_i */
-            orc_spmv(n, w->rowptr, w->col, w->val, ov, q);
-            orc_spmv(n, w->rowptr, w->col, w->val, u, wv);
+            MV(ov, q);
+            MV(u, wv);
         } else {
             /* q_i = As_i + beta_i l_{i-1}   (Eq. q) */
             ORC_ROWS
@@ -401,12 +472,12 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
         for (int64_t j = 0; j < n; ++j) x[j] = fma(alpha, p[j], x[j]) + z[j];
         if (rr_step) {
             /* Alg. 5 replacement: r = b - A x, l_i = A t_i (R9), g = A y, s = A r */
-            orc_spmv(n, w->rowptr, w->col, w->val, x, Aw);
+            MV(x, Aw);
             ORC_ROWS
             for (int64_t j = 0; j < n; ++j) r[j] = w->b[j] - Aw[j];
-            orc_spmv(n, w->rowptr, w->col, w->val, t, l);
-            orc_spmv(n, w->rowptr, w->col, w->val, y, g);
-            orc_spmv(n, w->rowptr, w->col, w->val, r, s);
+            MV(t, l);
+            MV(y, g);
+            MV(r, s);
             res->rr_steps++;
         } else {
             /* r_{i+1} = r_i - alpha_i o_i - y_{i+1} */
@@ -415,7 +486,7 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
             if (pipelined) {
                 /* Aw_i; l_i = q_i - Aw_i (Eq. l); g_{i+1} = zeta As_i + eta g_i - alpha Aw_i (Eq. g);
                    s_{i+1} = s_i - alpha q_i - g_{i+1} (Eq. sip1) */
-                orc_spmv(n, w->rowptr, w->col, w->val, wv, Aw);
+                MV(wv, Aw);
                 ORC_ROWS
                 for (int64_t j = 0; j < n; ++j) l[j] = q[j] - Aw[j];
                 ORC_ROWS
@@ -439,11 +510,10 @@ static int run_once(orc_ws* w, const orc_opts* o, double thresh, double r0ref, i
  * the first run stops there and state (SV_COUNT*n doubles, slot-major) and
  * scalars (SC_COUNT doubles) receive the dump.
  */
-int orc_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
-              const double* b, double* x, const orc_opts* o,
-              double* hist, int hist_cap, int* hist_len, double* scal_hist,
-              double* state, double* scalars, orc_result* res)
+static int solve_runs(orc_ws* w, double* x, const orc_opts* o, double* hist, int hist_cap, int* hist_len,
+                      double* scal_hist, double* state, double* scalars, orc_result* res)
 {
+    const int64_t n = w->n;
     memset(res, 0, sizeof(*res));
     if (hist_len) *hist_len = 0;
     int hl = 0;
@@ -451,28 +521,26 @@ int orc_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double
         res->status = ORC_ERR_ARG;
         return ORC_ERR_ARG;
     }
-    orc_ws w;
-    w.n = n; w.rowptr = rowptr; w.col = col; w.val = val; w.b = b;
     for (int k = 0; k < SV_COUNT; ++k) {
-        if (k == SV_X) { w.v[k] = x; continue; }
-        w.v[k] = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        if (k == SV_X) { w->v[k] = x; continue; }
+        w->v[k] = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     }
-    double r0 = orc_true_residual(n, rowptr, col, val, b, x);
+    double r0 = ws_true_residual(w, x);
     res->r0_norm = r0;
     const double thresh = o->tol * r0;
     const double r0ref = (r0 > 0.0) ? r0 : 1.0;
     int status = ORC_OK, total = 0, dumped = 0;
     for (int run = 0;; ++run) {
         int its = 0;
-        status = run_once(&w, o, thresh, r0ref, o->maxit - total, run == 0, hist, hist_cap, &hl,
+        status = run_once(w, o, thresh, r0ref, o->maxit - total, run == 0, hist, hist_cap, &hl,
                           scal_hist, &its, res, (o->dump_iter >= 0) ? scalars : NULL, &dumped);
         total += its;
         if (dumped) {
-            if (state) for (int k = 0; k < SV_COUNT; ++k) memcpy(state + (size_t)k * n, w.v[k], sizeof(double) * (size_t)n);
+            if (state) for (int k = 0; k < SV_COUNT; ++k) memcpy(state + (size_t)k * n, w->v[k], sizeof(double) * (size_t)n);
             break;
         }
         if (status != ORC_OK) break;
-        double tr = orc_true_residual(n, rowptr, col, val, b, x);
+        double tr = ws_true_residual(w, x);
         res->rel_res_true = tr / r0ref;
         if (tr <= thresh || run >= o->max_restarts) {
             if (tr > thresh) status = ORC_NOT_CONVERGED;
@@ -481,12 +549,43 @@ int orc_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double
         if (total >= o->maxit) { status = ORC_NOT_CONVERGED; break; }
         res->restarts++;
     }
-    if (!dumped) res->rel_res_true = orc_true_residual(n, rowptr, col, val, b, x) / r0ref;
+    if (!dumped) res->rel_res_true = ws_true_residual(w, x) / r0ref;
     res->iterations = total;
     res->status = status;
     if (hist_len) *hist_len = hl;
-    for (int k = 0; k < SV_COUNT; ++k) if (k != SV_X) free(w.v[k]);
+    for (int k = 0; k < SV_COUNT; ++k) if (k != SV_X) free(w->v[k]);
     return status;
+}
+
+int orc_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+              const double* b, double* x, const orc_opts* o,
+              double* hist, int hist_cap, int* hist_len, double* scal_hist,
+              double* state, double* scalars, orc_result* res)
+{
+    orc_ws w;
+    memset(&w, 0, sizeof(w));
+    w.n = n; w.rowptr = rowptr; w.col = col; w.val = val; w.b = b;
+    w.mv = mv_whole; w.dot = dot_whole; w.ctx = &w;
+    return solve_runs(&w, x, o, hist, hist_cap, hist_len, scal_hist, state, scalars, res);
+}
+
+/*
+ * The same runs over one block of rows of a row-partitioned system (the
+ * setting of Section 3: every process owns some rows of A and the same rows
+ * of every vector).  n_local, b and x are the block's; mv(ctx, x, y) must set
+ * y = (A x) on the block's rows and dot(ctx, x, y) must return the inner
+ * product over all rows, both given the block's parts of x and y.  With
+ * exact inner products and every row summed in CSR order the iterates are
+ * those of orc_solve, bit for bit.
+ */
+int orc_solve_hooked(int64_t n_local, const double* b, double* x, const orc_opts* o, orc_mv_fn mv, orc_dot_fn dot,
+                     void* ctx, double* hist, int hist_cap, int* hist_len, double* scal_hist, orc_result* res)
+{
+    orc_ws w;
+    memset(&w, 0, sizeof(w));
+    w.n = n_local; w.b = b;
+    w.mv = mv; w.dot = dot; w.ctx = ctx;
+    return solve_runs(&w, x, o, hist, hist_cap, hist_len, scal_hist, NULL, NULL, res);
 }
 
 /* ---- formats ----------------------------------------------------------- */
