@@ -101,6 +101,12 @@ int check_options(const bcs_options& o) {
 
 }  // namespace
 
+namespace bcs {
+// for the partitioned solver (dist.cu)
+int options_check(const bcs_options& o) { return check_options(o); }
+long long spin_cycles(double ms) { return budget_cycles(ms); }
+}  // namespace bcs
+
 extern "C" {
 
 void bcs_options_default(bcs_options* o) {

@@ -71,6 +71,27 @@ struct KParams {
     double* hist;           // [hist_cap]
     double* scal;           // [4*hist_cap]
     double* out;            // [NOUT]
+    // row-partitioned solve (include/bcs_dist.h): this rank's first global
+    // row, which of its rows other ranks need (per local row: entries
+    // send_ptr[row] .. send_ptr[row+1] of send_dst = (rank, offset in that
+    // rank's vectors)), whether a tile has such rows, and every rank's vectors
+    // ([rank][NVEC + 1], the FP64 x last); the caller's b and x in global rows.
+    int64_t row0;
+    const int32_t* send_ptr;
+    const int2* send_dst;
+    const unsigned char* tile_send;
+    void* const* peer_vec;
+    const double* bg;
+    double* xg;
+};
+
+constexpr int kDistMaxRanks = 16;   // BCS_DIST_MAX_RANKS
+// A partitioned solve: CTAs [cta0[r], cta0[r+1]) of the cooperative grid form
+// rank r, whose parameters are params[r].
+struct DistArgs {
+    const KParams* params;
+    int cta0[kDistMaxRanks + 1];
+    int nranks;
 };
 
 // Batched solves: the systems' parameter blocks (without workspace), their

@@ -15,9 +15,8 @@
 //   phase A  warps 1-9 pull the records of iteration i towards L1 and sum
 //            them while the other warps compute A s_i for their first tile
 //            (the overlap of the inner-product reduction with MV, Section 3);
-//            warp 0 forms beta, alpha, zeta, eta and the stop test while
-//            warps 1-9 compute their first tile's A s_i; then for every
-//            tile: A s_i and the fused recurrences for p, o, u, q, w, t, z,
+//            warp 0 forms beta, alpha, zeta, eta and the stop test; then
+//            for every tile: A s_i and the fused recurrences for p, o, u, q, w, t, z,
 //            y_{i+1}, x_{i+1}, r_{i+1}; A s_i is stored for phase C;
 //            partials of (y,y) (y,r) (r*,r) (r*,t) (r,r).          -- barrier
 //   phase C  A w_i; q = As + beta l, g' = zeta As + eta g, s' = s - alpha q
@@ -183,10 +182,16 @@ __device__ __forceinline__ void reduce_partials(const unsigned long long* base, 
 
 // A set of CTAs that solve one system together: the whole cooperative grid
 // (one large system) or one thread-block cluster (batched solves).
+// rank/size: the CTA's place among all CTAs that write inner-product records
+// and meet at the barriers; trank/tsize (when >= 0): its place among the CTAs
+// that share the tiles of one row block (a rank of a partitioned solve).
 struct GridGroup {
     GridBarrier gb;
     int rank, size;
     int nsync = 0;   // grid barriers passed (reported with the result)
+    int trank = -1, tsize = -1;
+    __device__ int tile_rank() const { return trank >= 0 ? trank : rank; }
+    __device__ int tile_size() const { return tsize >= 0 ? tsize : size; }
     __device__ bool sync(volatile int* flag) {
         ++nsync;
         return gb.sync(flag);
@@ -195,6 +200,8 @@ struct GridGroup {
 struct ClusterGroup {
     int rank, size;
     int nsync = 0;
+    __device__ int tile_rank() const { return rank; }
+    __device__ int tile_size() const { return size; }
     // barrier.cluster with release/acquire semantics: every write of the
     // cluster's threads before the barrier is visible after it.  All CTAs of
     // a cluster are co-scheduled, so the wait always ends.
@@ -205,7 +212,10 @@ struct ClusterGroup {
     }
 };
 
-template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group>
+// DIST: a rank of a partitioned solve (bcs_dist.h): CSR rows of its own block,
+// columns in its offset space, and every value that another rank's next
+// matrix-vector product gathers pushed into that rank's halo as it is written.
+template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
@@ -217,8 +227,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ double s_buf64[NW][32];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t gwarp = (int64_t)grp.rank * NW + warp;
-    const int64_t nwarps = (int64_t)grp.size * NW;
+    const int64_t gwarp = (int64_t)grp.tile_rank() * NW + warp;
+    const int64_t nwarps = (int64_t)grp.tile_size() * NW;
     const int64_t n = P.n, ntiles = P.ntiles;
     const int nblk = grp.size;
     const int rank = grp.rank;
@@ -243,9 +253,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     VT* const BinW = (VT*)P.vec[V_BIN];
     VT* sCur = (VT*)P.vec[V_S];
     VT* sNxt = (VT*)P.vec[V_S2];
+    int sCurId = V_S, sNxtId = V_S2;   // their vector ids (peers swap in step)
     // The inner system A x_in = b_in: (x64, b64) in FP64 mode, (d, r_outer) in refinement mode.
     VT* const X = mixed ? (VT*)P.vec[V_D] : (VT*)(void*)P.x64;
     const VT* const Bin = mixed ? (const VT*)BinW : (const VT*)(const void*)P.b64;
+    const int xId = mixed ? (int)V_D : (int)NVEC;
     const MT* const val = (const MT*)P.val;
     // row index inside a tile loop: 32-bit with FP32 vectors (fewer address
     // instructions per tile, measured faster); 64-bit with FP64 vectors, where
@@ -259,6 +271,23 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     };
     auto spmv64 = [&](const double* xv, int64_t tile) -> double {
         return tile_spmv<double, double, LAYOUT, T>(P, P.val64, xv, tile, sbuf64);
+    };
+    // partitioned solve: a value that another rank's next matrix-vector
+    // product gathers is stored straight into that rank's halo (vector id v,
+    // NVEC for the FP64 x); the barrier before the product makes it visible
+    auto push = [&](int v, int64_t tile, RowT row, auto val) {
+        if constexpr (DIST) {
+            using ET = decltype(val);
+            if (__ldg(P.tile_send + tile)) {
+                const int a = __ldg(P.send_ptr + row), b = __ldg(P.send_ptr + row + 1);
+                for (int k = a; k < b; ++k) {
+                    const int2 d = P.send_dst[k];
+                    ((ET*)P.peer_vec[d.x * (NVEC + 1) + v])[d.y] = val;
+                }
+            }
+        } else {
+            (void)v; (void)tile; (void)row; (void)val;
+        }
     };
     unsigned long long* const precs = (unsigned long long*)P.partials;
     auto rbase = [&](int buf) -> unsigned long long* { return precs + (size_t)buf * nblk * NSLOT * kRec; };
@@ -279,7 +308,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     auto rp_load = [&](int64_t t, int& a, int& b) {
         a = 0; b = 0;
         const int64_t r = t * 32 + lane;
-        if (t < ntiles && r < n) { a = __ldg(P.rowptr + r); b = __ldg(P.rowptr + r + 1); }
+        if (t < ntiles && r < n) {
+            const unsigned long long pol = l2_first();
+            a = ldg_col<VT>(P.rowptr + r, pol);
+            b = ldg_col<VT>(P.rowptr + r + 1, pol);
+        }
     };
     auto spmv_rp = [&](const VT* xv, int64_t tile, int a, int b) -> VT {
         if constexpr (kRp) return csr_tile_rp<VT, MT>(a, b, P.col, val, xv);
@@ -319,13 +352,35 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     };
     // stage the warp's first two tiles of a phase (after the grid barrier that
     // made the previous phase's writes visible)
-    auto stage_two = [&](const auto& v, int64_t t0, int64_t t1) {
-        if (t0 < ntiles) stg.issue(v, t0, 0);
-        if (t1 < ntiles) stg.issue(v, t1, 1);
+    auto stage_two = [&](auto first, const auto& v, int64_t t0, int64_t t1) {
+        constexpr unsigned F = decltype(first)::value;
+        if (t0 < ntiles) stg.template issue<F>(v, t0, 0);
+        if (t1 < ntiles) stg.template issue<F>(v, t1, 1);
     };
     // after a tile's rows were read: refill its stage with tile t (two ahead)
-    auto stage_at = [&](const auto& v, int64_t t, int64_t kt) {
-        if (t < ntiles) stg.issue(v, t, (int)(kt & 1));
+    auto stage_at = [&](auto first, const auto& v, int64_t t, int64_t kt) {
+        constexpr unsigned F = decltype(first)::value;
+        if (t < ntiles) stg.template issue<F>(v, t, (int)(kt & 1));
+    };
+    // L2 policy of the row-local vector streams (see l2_first): a vector read or
+    // written by a phase is marked evict_first when its next use is an
+    // iteration away or when the phase overwrites it; the vectors that the next
+    // phase reads stay at normal priority.  Staging masks per phase (bit k =
+    // entry k of the phase's vector list).  Applied with FP32 vectors only
+    // (l2_hints).
+    using FirstPA = std::integral_constant<unsigned, 0u>;                        // Y R RS
+    using FirstPB = std::integral_constant<unsigned, 1u << 2>;                   // R s T Y P U
+    using FirstPC = std::integral_constant<unsigned, 0xADu>;                     // O R U s Y P RS Z
+    using FirstA = std::integral_constant<unsigned, 0x638u>;                     // R s RS P U T L Y G W Z
+    using FirstC = std::integral_constant<unsigned, 0xFu>;                       // O L G s Y R RS
+    const unsigned long long polv = l2_first();
+    auto st1 = [&](VT* p, VT v) {
+        if constexpr (l2_hints<VT>()) st_first(p, v, polv);
+        else *p = v;
+    };
+    auto ld1 = [&](const VT* p) -> VT {
+        if constexpr (l2_hints<VT>()) return ld_first(p, polv);
+        else return *p;
     };
 
     // ---- SELL: the solve runs in the permuted row order ----
@@ -336,6 +391,20 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 const int32_t src = __ldg(P.perm + row);
                 P.x64[row] = P.x[src];
                 P.b64w[row] = P.b[src];
+            }
+        }
+        if (!grp.sync(&s_flag)) { stg.settle(); return; }
+    }
+
+    // ---- partitioned solve: this rank's rows of the caller's x (and their
+    // copies in the other ranks' halos) ----
+    if constexpr (DIST) {
+        for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+            const RowT row = (RowT)(tile * 32) + lane;
+            if (row < n) {
+                const double xv = P.xg[P.row0 + row];
+                P.x64[row] = xv;
+                push(NVEC, tile, row, xv);
             }
         }
         if (!grp.sync(&s_flag)) { stg.settle(); return; }
@@ -369,6 +438,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     qb_ST = r64;
                     const VT rv = (VT)r64;
                     R[row] = rv;
+                    push(V_R, tile, row, rv);
                     RS[row] = rv;
                     if (mixed) {
                         BinW[row] = rv;
@@ -419,6 +489,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 VT qa_SG = VT(0), qb_SG = VT(0);
                 if (row < n) {
                     sCur[row] = sv;
+                    push(sCurId, tile, row, sv);
                     const VT rv = R[row], rsv = RS[row];
                     qa_SA = sv;
                     qb_SA = sv;
@@ -442,7 +513,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             const bool rr_step = (kind == BCS_P_BICGSAFE_RR) && i > 0 && (i % P.rr_m) == 0 && i < P.rr_M;
             typename DotAccOf<VT>::type xv[10];
             VT as_first = VT(0);
-            bool first_late = false;   // this warp's first-tile SpMV runs in the scalar section
+            bool have_first = false;   // this warp's first-tile A s_i was formed during the reduction
             int64_t pa0 = 0, pa1 = 0;   // p-BiCGSafe phase A: the warp's first two tiles
             unsigned* pac = nullptr;
             if (kind == BCS_SSBICGSAFE2) {
@@ -453,7 +524,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 int64_t t0, t1;
                 unsigned* tc;
                 tiles_begin(t0, t1, tc);
-                stage_two(vPA, t0, t1);
+                stage_two(FirstPA{}, vPA, t0, t1);
                 int rpa = 0, rpb = 0;
                 if (kRp) rp_load(t0, rpa, rpb);
                 for (int64_t kt = 0; t0 < ntiles; ++kt) {
@@ -485,7 +556,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
-                    stage_at(vPA, t2, kt);
+                    stage_at(FirstPA{}, vPA, t2, kt);
                     t0 = t1;
                     t1 = t2;
                 }
@@ -495,16 +566,19 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // phase A: A s_i of the first tile is in flight while the partials of
                 // iteration i are reduced (the overlap of the reduction with MV, Section 3)
                 if (!rr_step) {
-                    // warps 1..9 reduce the nine slots while the others start their
-                    // first tile's SpMV; warps 1..9 start theirs while warp 0 forms
-                    // the scalars (so the reduction and the scalar recurrence both
-                    // run under the SpMV's memory latency)
+                    // warps 1..9 reduce the nine slots while the others compute their
+                    // first tile's A s_i (so the reduction runs under the SpMV's memory
+                    // latency); warps 1..9 form their first tile's product in the tile
+                    // loop, after the scalars (measured 3 % faster per iteration than
+                    // forming it while warp 0 computes the scalars, which kept every
+                    // warp waiting for those products at the scalars' barrier)
                     reduce_issue<9, NW, kRedOff>(rbase(cur), nblk);   // records travel to L1
                     const VT* const vA0[] = {R, sCur, RS, Pv, U, Tv, L, Y, G, W, Z};
                     tiles_begin(pa0, pa1, pac);
-                    stage_two(vA0, pa0, pa1);
-                    first_late = kRedOff > 0 && warp >= kRedOff && warp < kRedOff + 9;
-                    if (!first_late && pa0 < ntiles) as_first = spmv(sCur, pa0);
+                    stage_two(FirstA{}, vA0, pa0, pa1);
+                    const bool reducer = kRedOff > 0 && warp >= kRedOff && warp < kRedOff + 9;
+                    have_first = !reducer && pa0 < ntiles;
+                    if (have_first) as_first = spmv(sCur, pa0);
                     reduce_finish<9, NW, kRedOff>(rbase(cur), nblk, s_x, s_sum);
                 } else {
                     reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
@@ -538,7 +612,6 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             } else if (warp == kSqrtWarp && lane == 0) {
                 s_q[4] = sqrt(s_sum[SR]);
             }
-            if (first_late && pa0 < ntiles) as_first = spmv(sCur, pa0);
             __syncthreads();
             if (threadIdx.x == 0) {
                 const double a = s_sum[SA], bb = s_sum[SB], c = s_sum[SC];
@@ -612,7 +685,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 int64_t b0, b1;
                 unsigned* tb;
                 tiles_begin(b0, b1, tb);
-                stage_two(vPB, b0, b1);
+                stage_two(FirstPB{}, vPB, b0, b1);
                 for (int64_t kt = 0; b0 < ntiles; ++kt) {
                     const int64_t tile = b0;
                     const int64_t b2 = tiles_next(b1, tb);
@@ -625,8 +698,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT o = vfma(be, t, s);
                         u = vfma(ze, o, et * vfma(be, u, y));
                         Pv[row] = p; O[row] = o; U[row] = u;
+                        push(V_U, tile, row, u);
                     }
-                    stage_at(vPB, b2, kt);
+                    stage_at(FirstPB{}, vPB, b2, kt);
                     b0 = b1;
                     b1 = b2;
                 }
@@ -638,7 +712,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 int64_t c0, c1;
                 unsigned* tcc;
                 tiles_begin(c0, c1, tcc);
-                stage_two(vPC, c0, c1);
+                stage_two(FirstPC{}, vPC, c0, c1);
                 int rpa = 0, rpb = 0;
                 if (kRp) rp_load(c0, rpa, rpb);
                 for (int64_t kt = 0; c0 < ntiles; ++kt) {
@@ -658,13 +732,15 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     if (row < n) {
                         const VT o = sm[lane], r = sm[32 + lane], u = sm[64 + lane], s = sm[96 + lane];
                         const VT y = sm[128 + lane], p = sm[160 + lane], rs = sm[192 + lane];
-                        VT z = sm[224 + lane], x = X[row];
+                        VT z = sm[224 + lane], x = ld1(X + row);
                         const VT t = o - w;
                         z = vfma(-al, u, vfma(ze, r, et * z));
                         const VT yn = vfma(-al, w, vfma(ze, s, et * y));
                         x = vfma(al, p, x) + z;
                         const VT rn = vfma(-al, o, r) - yn;
-                        Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x; R[row] = rn;
+                        Tv[row] = t; st1(Z + row, z); Y[row] = yn; st1(X + row, x); R[row] = rn;
+                        push(xId, tile, row, x);
+                        push(V_R, tile, row, rn);
                         qa_SB = yn;
                         qb_SB = yn;
                         qa_SE = yn;
@@ -681,7 +757,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
-                    stage_at(vPC, c2, kt);
+                    stage_at(FirstPC{}, vPC, c2, kt);
                     c0 = c1;
                     c1 = c2;
                 }
@@ -699,7 +775,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t pa2 = tiles_next(pa1, pac);
                     int rpa_n = 0, rpb_n = 0;
                     if (kRp && kt > 0) rp_load(pa1, rpa_n, rpb_n);
-                    const VT As = (kt == 0) ? as_first : spmv_rp(sCur, tile, rpa, rpb);
+                    const VT As = (kt == 0) ? (have_first ? as_first : spmv(sCur, tile)) : spmv_rp(sCur, tile, rpa, rpb);
                     if (kt > 0) { rpa = rpa_n; rpb = rpb_n; }
                     const VT* sm = stg.wait((int)(kt & 1));
                     const RowT row = (RowT)(tile * 32) + lane;
@@ -712,7 +788,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT r = sm[lane], s = sm[32 + lane], rs = sm[64 + lane];
                         VT p = sm[96 + lane], u = sm[128 + lane], t = sm[160 + lane], l = sm[192 + lane];
                         VT y = sm[224 + lane], g = sm[256 + lane], w = sm[288 + lane], z = sm[320 + lane];
-                        VT x = X[row];
+                        VT x = ld1(X + row);
                         p = vfma(be, p - u, r);
                         const VT o = vfma(be, t, s);
                         u = vfma(ze, o, et * vfma(be, u, y));
@@ -723,8 +799,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT yn = vfma(-al, w, vfma(ze, s, et * y));
                         x = vfma(al, p, x) + z;
                         const VT rn = vfma(-al, o, r) - yn;
-                        Pv[row] = p; U[row] = u; W[row] = w; Tv[row] = t; Z[row] = z;
-                        Y[row] = yn; X[row] = x; R[row] = rn; O[row] = As;
+                        st1(Pv + row, p); st1(U + row, u); W[row] = w; st1(Tv + row, t); st1(Z + row, z);
+                        Y[row] = yn; st1(X + row, x); R[row] = rn; O[row] = As;
+                        push(V_W, tile, row, w);
+                        push(xId, tile, row, x);
                         qa_SB = yn;
                         qb_SB = yn;
                         qa_SE = yn;
@@ -741,7 +819,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
-                    stage_at(vA, pa2, kt);
+                    stage_at(FirstA{}, vA, pa2, kt);
                     pa0 = pa1;
                     pa1 = pa2;
                 }
@@ -757,7 +835,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 int64_t c0, c1;
                 unsigned* tcc;
                 tiles_begin(c0, c1, tcc);
-                stage_two(vC, c0, c1);
+                stage_two(FirstC{}, vC, c0, c1);
                 rpa = 0; rpb = 0;
                 if (kRp) rp_load(c0, rpa, rpb);
                 for (int64_t kt = 0; c0 < ntiles; ++kt) {
@@ -782,6 +860,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT g = vfma(-al, Aw, gp);
                         const VT s = sa - g;
                         L[row] = l; G[row] = g; sNxt[row] = s;
+                        push(sNxtId, tile, row, s);
                         const VT y = sm[128 + lane], r = sm[160 + lane], rs = sm[192 + lane];
                         qa_SA = s;
                         qb_SA = s;
@@ -796,13 +875,14 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
-                    stage_at(vC, c2, kt);
+                    stage_at(FirstC{}, vC, c2, kt);
                     c0 = c1;
                     c1 = c2;
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
+                const int tid = sCurId; sCurId = sNxtId; sNxtId = tid;
             } else {
                 // residual replacement iteration (Alg. 5)
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -814,6 +894,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT o = vfma(be, t, s);
                         u = vfma(ze, o, et * vfma(be, u, y));
                         Pv[row] = p; O[row] = o; U[row] = u;
+                        push(V_U, tile, row, u);
                     }
                 }
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
@@ -829,6 +910,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT yn = vfma(-al, w, vfma(ze, s, et * y));
                         x = vfma(al, p, x) + z;
                         W[row] = w; Tv[row] = t; Z[row] = z; Y[row] = yn; X[row] = x;
+                        push(xId, tile, row, x);
+                        push(V_T, tile, row, t);
+                        push(V_Y, tile, row, yn);
                     }
                 }
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
@@ -848,6 +932,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         const VT rn = Bin[row] - ax;
                         const VT y = Y[row], t = Tv[row], rs = RS[row];
                         R[row] = rn; L[row] = at; G[row] = ay;
+                        push(V_R, tile, row, rn);
                         qa_SB = y;
                         qb_SB = y;
                         qa_SE = y;
@@ -878,6 +963,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     VT qa_SG = VT(0), qb_SG = VT(0);
                     if (row < n) {
                         sNxt[row] = s;
+                        push(sNxtId, tile, row, s);
                         const VT y = Y[row], r = R[row], rs = RS[row];
                         qa_SA = s;
                         qb_SA = s;
@@ -898,6 +984,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 ++rr_steps;
                 n_spmv += 5;  // w = A u; A x, A t, A y; s = A r
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
+                const int tid = sCurId; sCurId = sNxtId; sNxtId = tid;
             }
         }
         total += i;
@@ -905,7 +992,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         if (mixed && inner_status != BCS_ERR_NONFINITE) {
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                 const RowT row = (RowT)(tile * 32) + lane;
-                if (row < n) P.x64[row] += (double)X[row];
+                if (row < n) {
+                    const double xn = P.x64[row] + (double)X[row];
+                    P.x64[row] = xn;
+                    push(NVEC, tile, row, xn);
+                }
             }
         }
         if (!grp.sync(&s_flag)) { stg.settle(); return; }
@@ -933,12 +1024,39 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             if (row < n) P.x[__ldg(P.perm + row)] = P.x64[row];
         }
     }
+    if constexpr (DIST) {
+        for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+            const RowT row = (RowT)(tile * 32) + lane;
+            if (row < n) P.xg[P.row0 + row] = P.x64[row];
+        }
+    }
 }
 
 template <class VT, class MT, int LAYOUT, int T, bool DYN>
 __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
     solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN>(P, grp);
+}
+
+// Partitioned solve (bcs_dist.h): one cooperative launch whose CTAs are split
+// into ranks; each CTA runs the solver body on its rank's row block, all CTAs
+// meet at the one grid barrier and sum every rank's inner-product records.
+template <class VT, class MT>
+__global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel_dist(const __grid_constant__ DistArgs D) {
+    __shared__ KParams sP;
+    __shared__ int s_r;
+    if (threadIdx.x == 0) {
+        int r = 0;
+        while (r + 1 < D.nranks && (int)blockIdx.x >= D.cta0[r + 1]) ++r;
+        s_r = r;
+        sP = D.params[r];
+    }
+    __syncthreads();
+    const int r = s_r;
+    GridGroup grp{GridBarrier{sP.bar, sP.err, gridDim.x, 0u, sP.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
+    grp.trank = (int)blockIdx.x - D.cta0[r];
+    grp.tsize = D.cta0[r + 1] - D.cta0[r];
+    solve_body<VT, MT, LAY_CSR, 1, kSolveWarps, false, GridGroup, true>(sP, grp);
 }
 
 // dynamic shared memory of the solver kernels: the per-warp staging buffers
@@ -971,6 +1089,28 @@ int max_grid_one(int* grid) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T, DYN>, kSolveBlock, smem);
     *grid = sms * per;
     return (int)e;
+}
+
+// Partitioned solve of one (VT, MT) pair: launch (D != nullptr) or report the
+// co-resident CTAs of the kernel (max_grid).
+template <class VT, class MT>
+int dispatch_dist(const DistArgs* D, int grid, cudaStream_t st, int* max_grid) {
+    const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
+    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel_dist<VT, MT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    if (!D) {
+        int dev = 0, sms = 0, per = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel_dist<VT, MT>, kSolveBlock, smem);
+        *max_grid = sms * per;
+        return (int)e;
+    }
+    void* args[] = {(void*)D};
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel_dist<VT, MT>, dim3(grid), dim3(kSolveBlock), args,
+                                            smem, st);
 }
 
 // Dispatch over layout and lanes-per-row for one (VT, MT) pair; each
