@@ -8,7 +8,8 @@ loudly when the compiled library is missing: there is no CPU fallback.
 Names follow the C ABI: csr_upload, matrix_info, matrix_export, spmv, dot,
 dot_noalloc, solver_create, solve, solve_host, get_history, get_scalars,
 solve_batched, Batch (bcs_batch_*), autotune, batch_autotune,
-autotune_sell_sigma, status_string.
+autotune_sell_sigma, status_string; include/bcs_dist.h: partition_rows,
+halo_plan, Dist (bcs_dist_*).
 """
 import ctypes
 import os
@@ -30,7 +31,8 @@ EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_mat
             "bcs_matrix_free", "bcs_solver_create", "bcs_solve", "bcs_solve_host", "bcs_get_history",
             "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_batch_create", "bcs_batch_solve",
             "bcs_batch_destroy", "bcs_autotune", "bcs_batch_autotune", "bcs_status_string",
-            "bcs_autotune_sell_sigma"]
+            "bcs_autotune_sell_sigma", "bcs_partition_rows", "bcs_halo_plan", "bcs_dist_create", "bcs_dist_solve",
+            "bcs_dist_get_history", "bcs_dist_get_scalars", "bcs_dist_info", "bcs_dist_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -95,6 +97,17 @@ def _load():
     L.bcs_batch_autotune.argtypes = [I, P, I, ctypes.POINTER(Options), I, P, I, ctypes.POINTER(I),
                                      ctypes.POINTER(Options), P]
     L.bcs_autotune_sell_sigma.argtypes = [P, I, I, I, P, I, P, ctypes.POINTER(I), ctypes.POINTER(P), P]
+    L.bcs_partition_rows.argtypes = [I64, P, I, P]
+    L.bcs_halo_plan.argtypes = [I64, P, P, I, P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                P, P, P, P, P, P]
+    L.bcs_dist_create.argtypes = [I64, I64, P, P, P, I, P, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
+    L.bcs_dist_solve.argtypes = [P, P, P, ctypes.POINTER(Result), P]
+    L.bcs_dist_get_history.argtypes = [P, P, I, ctypes.POINTER(I)]
+    L.bcs_dist_get_scalars.argtypes = [P, P, I, ctypes.POINTER(I)]
+    L.bcs_dist_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I)]
+    L.bcs_dist_destroy.argtypes = [P]
+    L.bcs_dist_destroy.restype = None
     L.bcs_status_string.argtypes = [I]
     L.bcs_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -453,3 +466,96 @@ def batch_autotune(Ms, kind="p-BiCGSafe", iters=20, stream=None, **kw):
     best = dict(kw)
     best.update(threads_per_row=out.threads_per_row, ctas_per_sm=out.ctas_per_sm)
     return best, [E[i].as_dict() for i in range(min(cnt.value, 16))]
+
+
+# ---- row-partitioned solve (include/bcs_dist.h) ------------------------------------------------
+
+def partition_rows(A, nparts):
+    """bcs_partition_rows: contiguous row blocks balanced by nnz + n; returns int64 bounds[nparts+1]."""
+    rp = _np(A.rowptr, np.int64)
+    out = np.zeros(nparts + 1, dtype=np.int64)
+    _check(lib.bcs_partition_rows(int(A.n), rp.ctypes.data, int(nparts), out.ctypes.data), "bcs_partition_rows")
+    return out
+
+
+def halo_plan(A, bounds, rank):
+    """bcs_halo_plan: rank's local columns (offsets from its first row: left halo negative, right halo
+    from npad = its rows rounded up to 32), halo columns and send list."""
+    rp, ci = _np(A.rowptr, np.int64), _np(A.col, np.int32)
+    bd = _np(bounds, np.int64)
+    nparts = len(bd) - 1
+    nl, nr, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    args = [int(A.n), rp.ctypes.data, ci.ctypes.data if len(ci) else None, nparts, bd.ctypes.data, int(rank),
+            ctypes.byref(nl), ctypes.byref(nr), ctypes.byref(ns)]
+    _check(lib.bcs_halo_plan(*args, None, None, None, None, None, None), "bcs_halo_plan")
+    nz = int(rp[bd[rank + 1]] - rp[bd[rank]])
+    out = dict(local_col=np.zeros(max(nz, 1), np.int32), left=np.zeros(max(nl.value, 1), np.int64),
+               right=np.zeros(max(nr.value, 1), np.int64), send_row=np.zeros(max(ns.value, 1), np.int32),
+               send_rank=np.zeros(max(ns.value, 1), np.int32), send_off=np.zeros(max(ns.value, 1), np.int64))
+    _check(lib.bcs_halo_plan(*args, *[out[k].ctypes.data for k in ["local_col", "left", "right", "send_row",
+                                                                   "send_rank", "send_off"]]), "bcs_halo_plan")
+    out["local_col"] = out["local_col"][:nz]
+    out["left"], out["right"] = out["left"][:nl.value], out["right"][:nr.value]
+    for k in ["send_row", "send_rank", "send_off"]:
+        out[k] = out[k][:ns.value]
+    out["row0"], out["nloc"] = int(bd[rank]), int(bd[rank + 1] - bd[rank])
+    out["npad"] = ((out["nloc"] + 31) // 32) * 32
+    return out
+
+
+class Dist:
+    """Row-partitioned solver (bcs_dist): nparts ranks, each a group of CTAs of one cooperative
+    launch with its own row block, halo and Krylov vectors.  A: host CSR (n, rowptr, col, val)."""
+
+    def __init__(self, A, nparts, kind="p-BiCGSafe", tol=1e-10, maxit=10000, bounds=None, **kw):
+        self.handle = None
+        self.n = int(A.n)
+        rp, ci, va = _np(A.rowptr, np.int64), _np(A.col, np.int32), _np(A.val, np.float64)
+        bd = None if bounds is None else _np(bounds, np.int64)
+        opts = options(**kw)
+        h = ctypes.c_void_p()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(lib.bcs_dist_create(self.n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data if len(ci) else None,
+                                   va.ctypes.data if len(va) else None, int(nparts),
+                                   None if bd is None else bd.ctypes.data, k, float(tol), int(maxit),
+                                   ctypes.byref(opts), ctypes.byref(h)), "bcs_dist_create")
+        self.handle = h.value
+        self.nparts = int(nparts)
+
+    def solve(self, b, x, stream=None):
+        _dvec(b, self.n, "b")
+        _dvec(x, self.n, "x")
+        r = Result()
+        code = lib.bcs_dist_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(r), _stream(stream))
+        if code == ERR_ARG or code == ERR_CUDA or code == ERR_OOM:
+            raise BcsError(code, "bcs_dist_solve")
+        return r.as_dict()
+
+    def history(self):
+        ln = ctypes.c_int()
+        _check(lib.bcs_dist_get_history(self.handle, None, 0, ctypes.byref(ln)), "bcs_dist_get_history")
+        out = np.zeros(max(ln.value, 1))
+        _check(lib.bcs_dist_get_history(self.handle, out.ctypes.data, ln.value, ctypes.byref(ln)),
+               "bcs_dist_get_history")
+        return out[:ln.value]
+
+    def scalars(self):
+        ln = ctypes.c_int()
+        _check(lib.bcs_dist_get_scalars(self.handle, None, 0, ctypes.byref(ln)), "bcs_dist_get_scalars")
+        out = np.zeros(4 * max(ln.value, 1))
+        _check(lib.bcs_dist_get_scalars(self.handle, out.ctypes.data, ln.value, ctypes.byref(ln)),
+               "bcs_dist_get_scalars")
+        return out[:4 * ln.value].reshape(-1, 4)
+
+    def info(self, rank):
+        v = [ctypes.c_int64() for _ in range(5)]
+        c = ctypes.c_int()
+        _check(lib.bcs_dist_info(self.handle, int(rank), *[ctypes.byref(t) for t in v], ctypes.byref(c)),
+               "bcs_dist_info")
+        return dict(row0=v[0].value, nloc=v[1].value, nleft=v[2].value, nright=v[3].value, nsend=v[4].value,
+                    ctas=c.value)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.bcs_dist_destroy(self.handle)
+            self.handle = None
