@@ -167,6 +167,31 @@ def error_vs_oracle(x, kind, gold):
             "oracle_iterations": g["iterations"], "oracle_outer_steps": g["outer_steps"]}
 
 
+def oracle_check_small(bcs, torch):
+    """Every method and precision on the 64x64 convection-diffusion system (4096 rows) against the
+    FP64 oracle's solve of the same method: max |x - x_oracle| over the whole vector, and whether x
+    is bit-identical (outside every timed region)."""
+    import oracle
+    import workloads as W
+    A = W.cd2d(64, 20.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A, stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    bd = torch.from_numpy(b).cuda()
+    out = {}
+    for kind in ["ssBiCGSafe2", "p-BiCGSafe", "p-BiCGSafe-rr"]:
+        ref = oracle.solve(A, b, kind=kind, tol=1e-10, maxit=10000, max_restarts=29)
+        for prec in ["fp64", "fp32", "bf16"]:
+            S = bcs.solver_create(M, kind, tol=1e-10, maxit=10000, precision=prec, max_outer=30)
+            x = torch.zeros_like(bd)
+            res = bcs.solve(S, bd, x)
+            xh = x.cpu().numpy()
+            out["%s_%s" % (kind, prec)] = {"status": res["status_name"], "iterations": res["iterations"],
+                                           "oracle_iterations": ref["iterations"],
+                                           "max_abs_err_vs_oracle": float(np.max(np.abs(xh - ref["x"]))),
+                                           "bit_identical": bool(np.array_equal(xh, ref["x"]))}
+    return out
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -569,6 +594,7 @@ def main():
             e["hbm"] = {"achieved": pgbs, "peak": hbm_peak, "unit": "GB/s", "frac": pgbs / hbm_peak}
             extras["%s_%s" % (kind, prec)] = e
 
+    small = oracle_check_small(bcs, torch) if rank == 0 else None
     line = None
     if rank == 0:
         cpu = None
@@ -603,7 +629,8 @@ def main():
                 "gpu_launches": a.steps,
                 "clocks": clocks,
                 "cpu_baseline": cpu,
-                "side_by_side": extras}
+                "side_by_side": extras,
+                "oracle_check_cd2d_64": small}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

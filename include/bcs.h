@@ -177,7 +177,8 @@ int bcs_matrix_export(bcs_matrix A, int32_t* rowptr, int32_t* col, double* val64
  * Rows are summed with fused multiply-adds; with one lane per row (and for
  * SELL) in storage order.  Asynchronous on stream.  The SELL path permutes x
  * and y through a scratch buffer owned by A, so SELL calls on one matrix
- * must not run concurrently on different streams.
+ * must not run concurrently on different streams.  BCS_ERR_ARG when x or y
+ * is not memory the device can read (see bcs_solve).
  */
 int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int vec_f32,
              int threads_per_row, void* stream);
@@ -195,6 +196,7 @@ int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int ve
  *   x, y     device vectors, FP64 when vec_f32 == 0, FP32 otherwise.
  *   result   host double receiving the value (a NaN or Inf operand gives NaN).
  * Synchronises the stream; allocates and frees a small device buffer.
+ * BCS_ERR_ARG when x or y is not memory the device can read (see bcs_solve).
  */
 int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result, void* stream);
 
@@ -246,6 +248,10 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
  * Solve A x = b.  b_dev: device double[n]; x_dev: device double[n], x_0 on
  * entry (the paper's experiments use x_0 = 0), the solution on exit.  Fills
  * *res (may be NULL).  Synchronises the stream before returning.
+ * Before any launch, b_dev and x_dev are checked with cudaPointerGetAttributes:
+ * device or managed memory, or page-locked host memory mapped for the
+ * device, is accepted; anything else (for example pageable host memory,
+ * which a kernel would read as a device address) gives BCS_ERR_ARG.
  */
 int bcs_solve(bcs_solver s, const double* b_dev, double* x_dev, bcs_result* res, void* stream);
 
@@ -294,7 +300,8 @@ int bcs_solve_batched(int nsys, const bcs_matrix* A, int kind, double tol, int m
  * resets, the persistent kernel, result download) in a CUDA graph that later
  * solves replay; if capture is not possible the sequence is issued directly.
  * bcs_batch_solve synchronises the stream and returns the worst status; a
- * handle is not thread-safe and runs one solve at a time.  The matrices must
+ * handle is not thread-safe and runs one solve at a time.  Every b[k], x[k]
+ * is checked as in bcs_solve (BCS_ERR_ARG before any launch).  The matrices must
  * outlive the handle.  bcs_batch_destroy(NULL) is ignored.
  * Errors: BCS_ERR_ARG (invalid arguments), BCS_ERR_OOM, BCS_ERR_CUDA.
  */

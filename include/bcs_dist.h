@@ -91,7 +91,7 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
  * in the original row order (x_dev holds x_0 on entry, x on exit); every
  * rank copies its rows in and out.  One cooperative launch on stream; fills
  * *res like bcs_solve (the counters are those of every rank, which agree).
- * Synchronises the stream.
+ * Synchronises the stream.  b_dev and x_dev are checked as in bcs_solve.
  */
 int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* res, void* stream);
 

@@ -102,6 +102,15 @@ int check_options(const bcs_options& o) {
 }  // namespace
 
 namespace bcs {
+bool device_reachable(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error the query may have recorded
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+           (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr);
+}
 // for the partitioned solver (dist.cu)
 int options_check(const bcs_options& o) { return check_options(o); }
 long long spin_cycles(double ms) { return budget_cycles(ms); }
@@ -333,6 +342,7 @@ static int launch(bcs_solver s, const double* b, double* x, cudaStream_t st) {
 int bcs_solve(bcs_solver s, const double* b_dev, double* x_dev, bcs_result* res, void* stream) {
     NvtxRange nv("bcs_solve");
     if (!s || (s->A->n > 0 && (!b_dev || !x_dev))) return BCS_ERR_ARG;
+    if (s->A->n > 0 && (!device_reachable(b_dev) || !device_reachable(x_dev))) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (s->A->n == 0) {
         if (res) { memset(res, 0, sizeof(*res)); }
@@ -517,6 +527,7 @@ int bcs_batch_solve(bcs_batch bt, const double* const* b, double* const* x, bcs_
     if (!bt || !b || !x) return BCS_ERR_ARG;
     for (int k = 0; k < bt->nsys; ++k) {
         if (bt->n[k] > 0 && (!b[k] || !x[k])) return BCS_ERR_ARG;
+        if (bt->n[k] > 0 && (!device_reachable(b[k]) || !device_reachable(x[k]))) return BCS_ERR_ARG;
         KParams& P = bt->hp[k];
         P.b = b[k];
         P.x = x[k];

@@ -392,6 +392,7 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
 int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* res, void* stream) {
     NvtxRange nv("bcs_dist_solve");
     if (!d || !b_dev || !x_dev) return BCS_ERR_ARG;
+    if (!device_reachable(b_dev) || !device_reachable(x_dev)) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     DistArgs D;
     memset(&D, 0, sizeof(D));

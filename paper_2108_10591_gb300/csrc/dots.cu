@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kBlock) k_dot_final(const unsigned long long* 
 
 extern "C" int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result, void* stream) {
     if (n < 0 || !result || (n > 0 && (!x || !y))) return BCS_ERR_ARG;
+    if (n > 0 && (!device_reachable(x) || !device_reachable(y))) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);

@@ -86,6 +86,12 @@ struct KParams {
 };
 
 constexpr int kDistMaxRanks = 16;   // BCS_DIST_MAX_RANKS
+
+// True when the current device can dereference p: device or managed memory, or
+// page-locked host memory mapped into the device's address space.  The entry
+// points that take device vectors refuse anything else (plain pageable host
+// memory would be read by a kernel as a device address).
+bool device_reachable(const void* p);
 // A partitioned solve: CTAs [cta0[r], cta0[r+1]) of the cooperative grid form
 // rank r, whose parameters are params[r].
 struct DistArgs {

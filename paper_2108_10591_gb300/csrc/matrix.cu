@@ -389,6 +389,7 @@ done:
 int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int vec_f32, int threads_per_row,
              void* stream) {
     if (!A || !x || !y) return BCS_ERR_ARG;
+    if (A->n > 0 && (!device_reachable(x) || !device_reachable(y))) return BCS_ERR_ARG;
     if (layout != BCS_LAYOUT_CSR && layout != BCS_LAYOUT_SELL) return BCS_ERR_ARG;
     if (!(A->layouts & layout)) return BCS_ERR_ARG;
     if (store != BCS_STORE_F64 && store != BCS_STORE_F32 && store != BCS_STORE_BF16) return BCS_ERR_ARG;

@@ -607,3 +607,58 @@ def test_barrier_timeout_is_reported_and_recoverable(env):
     assert res["status"] == bcs.ERR_TIMEOUT
     res, x, h, _ = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", max_ctas=8)
     assert res["status"] == 0 and orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
+
+
+def test_host_pointers_refused_before_any_launch(env):
+    """The C entry points check their vector pointers (cudaPointerGetAttributes) before
+    launching: pageable host memory is refused with BCS_ERR_ARG, page-locked host memory
+    mapped for the device is accepted, and the context stays usable."""
+    import ctypes
+    bcs, torch, orc = env
+    A = W.cd2d(16, 3.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A)
+    S = bcs.solver_create(M, "p-BiCGSafe", tol=1e-10, maxit=500)
+    r = bcs.Result()
+    bh, xh = np.ascontiguousarray(b), np.zeros(A.n)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    assert bcs.lib.bcs_solve(S.handle, bh.ctypes.data, xd.data_ptr(), ctypes.byref(r), None) == bcs.ERR_ARG
+    assert bcs.lib.bcs_solve(S.handle, bd.data_ptr(), xh.ctypes.data, ctypes.byref(r), None) == bcs.ERR_ARG
+    out = ctypes.c_double()
+    assert bcs.lib.bcs_dot(A.n, bh.ctypes.data, bd.data_ptr(), 0, ctypes.byref(out), None) == bcs.ERR_ARG
+    assert bcs.lib.bcs_spmv(M.handle, bcs.LAYOUT_CSR, bcs.STORE_F64, bh.ctypes.data, xd.data_ptr(), 0, 1,
+                            None) == bcs.ERR_ARG
+    bp = torch.from_numpy(b).pin_memory()
+    xp = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    assert bcs.lib.bcs_solve(S.handle, bp.data_ptr(), xp.data_ptr(), ctypes.byref(r), None) == bcs.OK
+    ref = orc.solve(A, b, kind="p-BiCGSafe", tol=1e-10, maxit=500, max_restarts=29)
+    assert np.array_equal(xp.numpy(), ref["x"])
+    res = bcs.solve(S, bd, xd)
+    assert res["status"] == 0 and np.array_equal(xd.cpu().numpy(), ref["x"])
+
+
+@pytest.mark.parametrize("name", ["cd2d_64", "cd3d_32"])
+def test_low_precision_first_inner_run_tracks_fp64_oracle(env, name):
+    """The first inner run of the refinement modes, iteration by iteration, against the FP64
+    oracle's residual history.  FP32 vectors and values round every operation to u = 2^-24 and
+    the Krylov recurrence amplifies an early perturbation by about 2 per iteration on these
+    systems, so the relative difference of iteration i stays below 16 u 2^i over the first
+    8 iterations (the measured differences are 10-50x below the bound).  BF16 matrix values
+    perturb A itself by u = 2^-9; that difference grows about linearly, below 16 u (i+1)."""
+    bcs, torch, orc = env
+    A = W.cd2d(64, 20.0) if name == "cd2d_64" else W.cd3d_upwind(32, 50.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A, stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    ref = orc.solve(A, b, kind="p-BiCGSafe", tol=0.0, maxit=8)
+    for prec, u, grow in [("fp32", 2.0 ** -24, lambda i: 2.0 ** i), ("bf16", 2.0 ** -9, lambda i: i + 1.0)]:
+        S = bcs.solver_create(M, "p-BiCGSafe", tol=1e-300, maxit=8, precision=prec, max_outer=1,
+                              inner_tol=1e-300, inner_stall=0, threads_per_row=1)
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bd)
+        bcs.solve(S, bd, x)
+        h = bcs.get_history(S)
+        assert len(h) == len(ref["hist"]) == 9
+        rel = np.abs(h - ref["hist"]) / ref["hist"]
+        for i in range(9):
+            assert rel[i] <= 16 * u * grow(i), (prec, i, rel[i])
