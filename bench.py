@@ -122,6 +122,11 @@ def args_parse():
                     help="cd3d_128 (the benchmark line); the others print a side measurement line")
     ap.add_argument("--tune", action="store_true", help="side workloads: autotune the layout / lanes per row first")
     ap.add_argument("--precond", default="none", choices=["none", "jacobi"], help="side workloads: preconditioner")
+    ap.add_argument("--big-ctas", type=int, default=-1,
+                    help="batch: CTAs per cluster of the second lane for the largest systems (0 = one lane; "
+                         "default: 8 with FP32/BF16 inner solves, where it was measured 10 %% faster, 0 in FP64, "
+                         "where the batch is throughput-bound and it was slower)")
+    ap.add_argument("--big-systems", type=int, default=0, help="batch: systems in the second lane (0 = automatic)")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed solves (no end-to-end, side-by-side or CPU legs): the command profiled by ncu")
     return ap.parse_args()
@@ -388,7 +393,8 @@ def side_batch(a, bcs, torch, dist, world, rank):
     mine = [order[k] for k in shard_systems(len(order), rank, world)]
     mats = [mats[k] for k in mine]
     Ms = [bcs.csr_upload(A, stores=bcs.STORE_F32 | bcs.STORE_BF16) for A in mats]
-    kw = dict(precision=a.precision, max_outer=30)
+    big = a.big_ctas if a.big_ctas >= 0 else (0 if a.precision == "fp64" else 8)
+    kw = dict(precision=a.precision, max_outer=30, big_ctas=big, big_systems=a.big_systems)
     if a.kind == "p-BiCGSafe-rr":
         kw["rr_m"] = 20
     tune = None
@@ -424,7 +430,8 @@ def side_batch(a, bcs, torch, dist, world, rank):
                               "last_finish": ends[-1], "p90_finish": ends[int(0.9 * (len(ends) - 1))]},
             "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "kind": a.kind,
                        "precision": a.precision, "batch_options": {k: kw[k] for k in kw
-                                                                    if k in ("threads_per_row", "ctas_per_sm")},
+                                                                    if k in ("threads_per_row", "ctas_per_sm",
+                                                                             "big_ctas", "big_systems")},
                        "parallelism": "systems sharded over ranks" if world > 1 else "single GPU"},
             "tune": tune}
 

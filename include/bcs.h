@@ -104,6 +104,13 @@ typedef struct {
                              2 = dynamic (warps claim tiles from a counter); FP64 results do not depend on
                              it, refinement-mode results may in the last bits */
     int precond;          /* BCS_PRECOND_NONE (default) or BCS_PRECOND_JACOBI (single-system solves) */
+    int big_ctas;         /* batched solves: 0 (default) = one lane; 2, 4, 8 or 16 = the largest systems
+                             are solved concurrently by a second persistent launch whose clusters have
+                             this many CTAs (larger than ctas_per_sm), so that the longest solves do not
+                             run alone on two CTAs at the end of the batch */
+    int big_systems;      /* batched solves with big_ctas: how many of the largest systems (by nnz + n)
+                             take the second lane, one cluster each; 0 = as many clusters of big_ctas as
+                             fit in a quarter of the device */
 } bcs_options;
 
 typedef struct {

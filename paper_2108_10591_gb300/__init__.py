@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("history_len", ctypes.c_int),
                 ("layout", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("max_ctas", ctypes.c_int), ("spin_budget_ms", ctypes.c_double), ("inner_maxit", ctypes.c_int),
-                ("inner_stall", ctypes.c_int), ("tile_order", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("inner_stall", ctypes.c_int), ("tile_order", ctypes.c_int), ("precond", ctypes.c_int),
+                ("big_ctas", ctypes.c_int), ("big_systems", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

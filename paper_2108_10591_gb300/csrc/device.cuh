@@ -76,6 +76,12 @@ __device__ __forceinline__ unsigned long long l2_first() {
     asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
+// Solves use the hints only when the vectors that the next phase re-reads fit
+// in L2 together (KParams::l2hint, decided on the host from the system size;
+// the kernels are instantiated with and without them, H): hints that cannot
+// keep the re-read set resident were measured to cost time, and so did a
+// run-time choice inside the tile loops (a branch per load, or both code
+// paths in the loop body).
 __device__ __forceinline__ int ldg_first(const int32_t* p, unsigned long long pol) {
     int v;
     asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
@@ -121,21 +127,22 @@ __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const uint16_t* p) {
     return __uint_as_float(((unsigned)__ldg((const unsigned short*)p)) << 16);
 }
-// The hints are used with FP32 vectors only: there the vectors that the next
-// phase re-reads fit in L2 together (8 x 8.4 MB on the 2.1M-row system) and
-// the hints cut the DRAM traffic of an iteration by a quarter.  With FP64
-// vectors that set is larger than L2 and the hints were measured to add
-// traffic, so FP64 solves load and store without them.
+// The hints are used with FP32 vectors only, and then only on systems whose
+// re-read set fits in L2 (8 x 8.4 MB on the 2.1M-row system: the hints cut
+// the DRAM traffic of an iteration by a quarter).  With FP64 vectors that
+// set is larger than L2 on the large systems and the hints were measured to
+// add traffic, so FP64 solves load and store without them.
 template <class VT>
 __host__ __device__ constexpr bool l2_hints() { return sizeof(VT) == 4; }
-template <class VT>
+// Matrix loads of a tile: H (compile time) = with the evict_first policy pol.
+template <bool H>
 __device__ __forceinline__ int ldg_col(const int32_t* p, unsigned long long pol) {
-    if constexpr (l2_hints<VT>()) return ldg_first(p, pol);
+    if constexpr (H) return ldg_first(p, pol);
     else return __ldg(p);
 }
-template <class VT, class MT>
+template <bool H, class VT, class MT>
 __device__ __forceinline__ VT ldg_val(const MT* p, unsigned long long pol) {
-    if constexpr (l2_hints<VT>()) return (VT)ldv_first(p, pol);
+    if constexpr (H) return (VT)ldv_first(p, pol);
     else return (VT)ldv(p);
 }
 
@@ -181,15 +188,15 @@ struct WarpStager {
     unsigned pending;          // bit s: stage s has a committed group not yet waited for
 
     // FIRST: bit k set = vector k is not read again before L2 drops it (evict_first)
-    template <unsigned FIRST = 0u, int K>
-    __device__ __forceinline__ void issue(const VT* const (&v)[K], int64_t tile, int stage) {
+    template <unsigned FIRST = 0u, bool H = false, int K>
+    __device__ __forceinline__ void issue(const VT* const (&v)[K], int64_t tile, int stage,
+                                          unsigned long long pol = 0ull) {
         const int lane = threadIdx.x & 31;
-        const unsigned long long pol = l2_first();
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             VT* const d = buf + (stage * kMaxStage + k) * 32 + lane;
             const VT* const src = v[k] + tile * 32 + lane;
-            if (l2_hints<VT>() && ((FIRST >> k) & 1u)) cp_async_elem_first(d, src, pol);
+            if (H && ((FIRST >> k) & 1u)) cp_async_elem_first(d, src, pol);
             else cp_async_elem(d, src);
         }
         cp_async_commit();
@@ -217,17 +224,16 @@ constexpr int kSpmvBatch = 8;  // entries per lane whose loads are in flight tog
 // T lanes of a group take strided entries of one row, then combine with a
 // butterfly; 32/T rows per pass, results transposed back through shared
 // memory so that lane k holds row row0+k.  Rows >= n yield 0.
-template <class VT, class MT, int T>
+template <class VT, class MT, int T, bool H>
 __device__ __forceinline__ VT csr_tile(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                        const MT* __restrict__ val, const VT* x, int64_t row0, int64_t n,
-                                       VT* s_buf) {
+                                       VT* s_buf, unsigned long long pol) {
     const int lane = threadIdx.x & 31;
     const int64_t row = row0 + lane;
-    const unsigned long long pol = l2_first();
     int rp0 = 0, rp1 = 0;
     if (row < n) {
-        rp0 = ldg_col<VT>(rowptr + row, pol);
-        rp1 = ldg_col<VT>(rowptr + row + 1, pol);
+        rp0 = ldg_col<H>(rowptr + row, pol);
+        rp1 = ldg_col<H>(rowptr + row + 1, pol);
     }
     if constexpr (T == 1) {
         // Batches of kSpmvBatch entries: all column and value loads of the batch are
@@ -240,8 +246,8 @@ __device__ __forceinline__ VT csr_tile(const int32_t* __restrict__ rowptr, const
 #pragma unroll
             for (int j = 0; j < kSpmvBatch; ++j) {
                 const bool in = k0 + j < rp1;
-                c[j] = in ? ldg_col<VT>(col + k0 + j, pol) : 0;
-                v[j] = in ? ldg_val<VT>(val + k0 + j, pol) : VT(0);
+                c[j] = in ? ldg_col<H>(col + k0 + j, pol) : 0;
+                v[j] = in ? ldg_val<H, VT>(val + k0 + j, pol) : VT(0);
             }
 #pragma unroll
             for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + j < rp1) ? x[c[j]] : VT(0);
@@ -260,7 +266,7 @@ __device__ __forceinline__ VT csr_tile(const int32_t* __restrict__ rowptr, const
             const int e = __shfl_sync(kFull, rp1, r);
             VT acc = VT(0);
 #pragma unroll 2
-            for (int k = b + sub; k < e; k += T) acc = vfma(ldg_val<VT>(val + k, pol), x[ldg_col<VT>(col + k, pol)], acc);
+            for (int k = b + sub; k < e; k += T) acc = vfma(ldg_val<H, VT>(val + k, pol), x[ldg_col<H>(col + k, pol)], acc);
 #pragma unroll
             for (int off = T / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
             if (sub == 0) s_buf[r] = acc;
@@ -276,11 +282,11 @@ __device__ __forceinline__ VT csr_tile(const int32_t* __restrict__ rowptr, const
 // slice is column-major, so each step reads 32 consecutive values and column
 // indices (fully coalesced); each lane sums its row in storage order with fma.
 // Padding (value 0, a valid column) leaves the sum unchanged.
-template <class VT, class MT>
+template <class VT, class MT, bool H>
 __device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ scol,
-                                        const MT* __restrict__ sval, const VT* x, int64_t slice) {
+                                        const MT* __restrict__ sval, const VT* x, int64_t slice,
+                                        unsigned long long pol) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long pol = l2_first();
     const int64_t b = __ldg(slice_ptr + slice), e = __ldg(slice_ptr + slice + 1);
     VT acc = VT(0);
     for (int64_t k0 = b + lane; k0 < e; k0 += 32 * kSpmvBatch) {  // batched as in csr_tile
@@ -289,8 +295,8 @@ __device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, c
 #pragma unroll
         for (int j = 0; j < kSpmvBatch; ++j) {
             const bool in = k0 + 32 * j < e;
-            c[j] = in ? ldg_col<VT>(scol + k0 + 32 * j, pol) : 0;
-            v[j] = in ? ldg_val<VT>(sval + k0 + 32 * j, pol) : VT(0);
+            c[j] = in ? ldg_col<H>(scol + k0 + 32 * j, pol) : 0;
+            v[j] = in ? ldg_val<H, VT>(sval + k0 + 32 * j, pol) : VT(0);
         }
 #pragma unroll
         for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + 32 * j < e) ? x[c[j]] : VT(0);
@@ -308,16 +314,16 @@ __device__ __forceinline__ VT sell_tile(const int64_t* __restrict__ slice_ptr, c
 // waits for them one entry at a time.  The long rows' sums are therefore in a
 // different order than a plain sequential loop (deterministic).
 constexpr int kLongRow = 32;
-template <class VT, class MT>
+template <class VT, class MT, bool H>
 __device__ __forceinline__ VT csr_tile_adaptive(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                                const MT* __restrict__ val, const VT* x, int64_t row0, int64_t n) {
+                                                const MT* __restrict__ val, const VT* x, int64_t row0, int64_t n,
+                                                unsigned long long pol) {
     const int lane = threadIdx.x & 31;
     const int64_t row = row0 + lane;
-    const unsigned long long pol = l2_first();
     int rp0 = 0, rp1 = 0;
     if (row < n) {
-        rp0 = ldg_col<VT>(rowptr + row, pol);
-        rp1 = ldg_col<VT>(rowptr + row + 1, pol);
+        rp0 = ldg_col<H>(rowptr + row, pol);
+        rp1 = ldg_col<H>(rowptr + row + 1, pol);
     }
     const bool lng = rp1 - rp0 > kLongRow;
     unsigned lmask = __ballot_sync(kFull, lng);
@@ -329,8 +335,8 @@ __device__ __forceinline__ VT csr_tile_adaptive(const int32_t* __restrict__ rowp
 #pragma unroll
         for (int j = 0; j < kSpmvBatch; ++j) {
             const bool in = k0 + j < send;
-            c[j] = in ? ldg_col<VT>(col + k0 + j, pol) : 0;
-            v[j] = in ? ldg_val<VT>(val + k0 + j, pol) : VT(0);
+            c[j] = in ? ldg_col<H>(col + k0 + j, pol) : 0;
+            v[j] = in ? ldg_val<H, VT>(val + k0 + j, pol) : VT(0);
         }
 #pragma unroll
         for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + j < send) ? x[c[j]] : VT(0);
@@ -349,8 +355,8 @@ __device__ __forceinline__ VT csr_tile_adaptive(const int32_t* __restrict__ rowp
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const bool in = k0 + 32 * j < e;
-                c[j] = in ? ldg_col<VT>(col + k0 + 32 * j, pol) : 0;
-                v[j] = in ? ldg_val<VT>(val + k0 + 32 * j, pol) : VT(0);
+                c[j] = in ? ldg_col<H>(col + k0 + 32 * j, pol) : 0;
+                v[j] = in ? ldg_val<H, VT>(val + k0 + 32 * j, pol) : VT(0);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) xv[j] = (k0 + 32 * j < e) ? x[c[j]] : VT(0);
@@ -368,10 +374,9 @@ __device__ __forceinline__ VT csr_tile_adaptive(const int32_t* __restrict__ rowp
 // CSR tile, one lane per row, with the lane's row range [rp0, rp1) already
 // loaded (rows >= n: an empty range): the same entries, order and fmas as
 // csr_tile<VT, MT, 1>.
-template <class VT, class MT>
+template <class VT, class MT, bool H>
 __device__ __forceinline__ VT csr_tile_rp(int rp0, int rp1, const int32_t* __restrict__ col,
-                                          const MT* __restrict__ val, const VT* x) {
-    const unsigned long long pol = l2_first();
+                                          const MT* __restrict__ val, const VT* x, unsigned long long pol) {
     VT acc = VT(0);
     for (int k0 = rp0; k0 < rp1; k0 += kSpmvBatch) {
         int c[kSpmvBatch];
@@ -379,8 +384,8 @@ __device__ __forceinline__ VT csr_tile_rp(int rp0, int rp1, const int32_t* __res
 #pragma unroll
         for (int j = 0; j < kSpmvBatch; ++j) {
             const bool in = k0 + j < rp1;
-            c[j] = in ? ldg_col<VT>(col + k0 + j, pol) : 0;
-            v[j] = in ? ldg_val<VT>(val + k0 + j, pol) : VT(0);
+            c[j] = in ? ldg_col<H>(col + k0 + j, pol) : 0;
+            v[j] = in ? ldg_val<H, VT>(val + k0 + j, pol) : VT(0);
         }
 #pragma unroll
         for (int j = 0; j < kSpmvBatch; ++j) xv[j] = (k0 + j < rp1) ? x[c[j]] : VT(0);
@@ -390,14 +395,14 @@ __device__ __forceinline__ VT csr_tile_rp(int rp0, int rp1, const int32_t* __res
     }
     return acc;
 }
-template <class VT, class MT, int LAYOUT, int T>
+// H: matrix loads with the evict_first policy (FP32/BF16 vectors only)
+template <class VT, class MT, int LAYOUT, int T, bool H = false>
 __device__ __forceinline__ VT tile_spmv(const KParams& P, const MT* val, const VT* x, int64_t tile, VT* s_buf) {
-    if constexpr (LAYOUT == LAY_SELL) {
-        return sell_tile<VT, MT>(P.slice_ptr, P.col, val, x, tile);
-    } else {
-        if constexpr (T == 0) return csr_tile_adaptive<VT, MT>(P.rowptr, P.col, val, x, tile * 32, P.n);
-        else return csr_tile<VT, MT, T>(P.rowptr, P.col, val, x, tile * 32, P.n, s_buf);
-    }
+    constexpr bool kH = H && l2_hints<VT>();
+    const unsigned long long pol = kH ? l2_first() : 0ull;
+    if constexpr (LAYOUT == LAY_SELL) return sell_tile<VT, MT, kH>(P.slice_ptr, P.col, val, x, tile, pol);
+    else if constexpr (T == 0) return csr_tile_adaptive<VT, MT, kH>(P.rowptr, P.col, val, x, tile * 32, P.n, pol);
+    else return csr_tile<VT, MT, T, kH>(P.rowptr, P.col, val, x, tile * 32, P.n, s_buf, pol);
 }
 
 }  // namespace bcs

@@ -71,6 +71,7 @@ struct KParams {
     double* hist;           // [hist_cap]
     double* scal;           // [4*hist_cap]
     double* out;            // [NOUT]
+    int l2hint;             // launch the L2-hinted kernel (FP32 vectors, CSR, one lane per row; see l2_hint_pays)
     // row-partitioned solve (include/bcs_dist.h): this rank's first global
     // row, which of its rows other ranks need (per local row: entries
     // send_ptr[row] .. send_ptr[row+1] of send_dst = (rank, offset in that
@@ -92,6 +93,9 @@ constexpr int kDistMaxRanks = 16;   // BCS_DIST_MAX_RANKS
 // points that take device vectors refuse anything else (plain pageable host
 // memory would be read by a kernel as a device address).
 bool device_reachable(const void* p);
+// Whether a solve with FP32 vectors of `rows` padded rows (all ranks together)
+// should mark its single-use streams evict_first (KParams::l2hint).
+bool l2_hint_pays(int vt_f32, int64_t rows);
 // A partitioned solve: CTAs [cta0[r], cta0[r+1]) of the cooperative grid form
 // rank r, whose parameters are params[r].
 struct DistArgs {
@@ -150,6 +154,7 @@ struct bcs_solver_s {
     double tol = 0;
     bcs_options opt;
     int vt_f32 = 0, valtype = 0, layout = 0, tpr = 1, dyn = 0;
+    int l2hint = 0;               // KParams::l2hint
     int grid = 0;
     size_t vbytes = 0;
     void* vecmem = nullptr;       // NVEC vectors
@@ -177,6 +182,16 @@ struct bcs_batch_s {
     int nsys = 0, vt_f32 = 0, valtype = 0, tpr = 1, nclusters = 0;
     std::vector<int64_t> n;
     bcs::BatchArgs B;
+    // the second lane (bcs_options::big_ctas): the largest systems, bigger clusters,
+    // launched on a side stream concurrently with the first lane
+    int nbig = 0, nclusters2 = 0;
+    bcs::BatchArgs B2;
+    int* dctl2 = nullptr;
+    char* ws2 = nullptr;
+    double* parts2 = nullptr;
+    int* herr2 = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     bcs::KParams* hp = nullptr;   // pinned [nsys]
     bcs::KParams* dsys = nullptr;
     int* dorder = nullptr;

@@ -215,7 +215,9 @@ struct ClusterGroup {
 // DIST: a rank of a partitioned solve (bcs_dist.h): CSR rows of its own block,
 // columns in its offset space, and every value that another rank's next
 // matrix-vector product gathers pushed into that rank's halo as it is written.
-template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false>
+// H: the L2 evict_first policy on the matrix and the single-use vector
+// streams (FP32/BF16 vectors; instantiated for CSR with one lane per row).
+template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false, bool H = false>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
@@ -267,7 +269,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     double* const sbuf64 = s_buf64[warp];
 
     auto spmv = [&](const VT* xv, int64_t tile) -> VT {
-        return tile_spmv<VT, MT, LAYOUT, T>(P, val, xv, tile, sbuf);
+        return tile_spmv<VT, MT, LAYOUT, T, H>(P, val, xv, tile, sbuf);
     };
     auto spmv64 = [&](const double* xv, int64_t tile) -> double {
         return tile_spmv<double, double, LAYOUT, T>(P, P.val64, xv, tile, sbuf64);
@@ -305,17 +307,19 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     // starts with its column and value loads (in FP64 mode the two extra
     // registers cost more than the latency they hide)
     constexpr bool kRp = (LAYOUT == LAY_CSR && T == 1 && sizeof(VT) == 4);
+    // L2 policy of the matrix and of the single-use vector streams (see l2_first)
+    constexpr bool kH = H && l2_hints<VT>();
+    const unsigned long long polv = kH ? l2_first() : 0ull;
     auto rp_load = [&](int64_t t, int& a, int& b) {
         a = 0; b = 0;
         const int64_t r = t * 32 + lane;
         if (t < ntiles && r < n) {
-            const unsigned long long pol = l2_first();
-            a = ldg_col<VT>(P.rowptr + r, pol);
-            b = ldg_col<VT>(P.rowptr + r + 1, pol);
+            a = __ldg(P.rowptr + r);
+            b = __ldg(P.rowptr + r + 1);
         }
     };
     auto spmv_rp = [&](const VT* xv, int64_t tile, int a, int b) -> VT {
-        if constexpr (kRp) return csr_tile_rp<VT, MT>(a, b, P.col, val, xv);
+        if constexpr (kRp) return csr_tile_rp<VT, MT, kH>(a, b, P.col, val, xv, polv);
         else return spmv(xv, tile);
     };
     // Tile order of an iteration phase.  Static: tile t belongs to warp t mod
@@ -354,32 +358,33 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     // made the previous phase's writes visible)
     auto stage_two = [&](auto first, const auto& v, int64_t t0, int64_t t1) {
         constexpr unsigned F = decltype(first)::value;
-        if (t0 < ntiles) stg.template issue<F>(v, t0, 0);
-        if (t1 < ntiles) stg.template issue<F>(v, t1, 1);
+        if (t0 < ntiles) stg.template issue<F, kH>(v, t0, 0, polv);
+        if (t1 < ntiles) stg.template issue<F, kH>(v, t1, 1, polv);
     };
     // after a tile's rows were read: refill its stage with tile t (two ahead)
     auto stage_at = [&](auto first, const auto& v, int64_t t, int64_t kt) {
         constexpr unsigned F = decltype(first)::value;
-        if (t < ntiles) stg.template issue<F>(v, t, (int)(kt & 1));
+        if (t < ntiles) stg.template issue<F, kH>(v, t, (int)(kt & 1), polv);
     };
     // L2 policy of the row-local vector streams (see l2_first): a vector read or
     // written by a phase is marked evict_first when its next use is an
     // iteration away or when the phase overwrites it; the vectors that the next
     // phase reads stay at normal priority.  Staging masks per phase (bit k =
     // entry k of the phase's vector list).  Applied with FP32 vectors only
-    // (l2_hints).
+    // (l2_hints), and evict_first only when the solve's re-read set fits in L2
+    // (KParams::l2hint; otherwise the same streams carry evict_normal).
     using FirstPA = std::integral_constant<unsigned, 0u>;                        // Y R RS
     using FirstPB = std::integral_constant<unsigned, 1u << 2>;                   // R s T Y P U
     using FirstPC = std::integral_constant<unsigned, 0xADu>;                     // O R U s Y P RS Z
     using FirstA = std::integral_constant<unsigned, 0x638u>;                     // R s RS P U T L Y G W Z
     using FirstC = std::integral_constant<unsigned, 0xFu>;                       // O L G s Y R RS
-    const unsigned long long polv = l2_first();
+
     auto st1 = [&](VT* p, VT v) {
-        if constexpr (l2_hints<VT>()) st_first(p, v, polv);
+        if constexpr (kH) st_first(p, v, polv);
         else *p = v;
     };
     auto ld1 = [&](const VT* p) -> VT {
-        if constexpr (l2_hints<VT>()) return ld_first(p, polv);
+        if constexpr (kH) return ld_first(p, polv);
         else return *p;
     };
 
@@ -1032,10 +1037,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     }
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false>
 __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
-    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN>(P, grp);
+    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN, GridGroup, false, H>(P, grp);
 }
 
 // Partitioned solve (bcs_dist.h): one cooperative launch whose CTAs are split
@@ -1065,15 +1070,15 @@ constexpr size_t stage_smem_bytes() {
     return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT);
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false>
 int launch_one(const KParams& P, int grid, cudaStream_t st) {
     void* args[] = {(void*)&P};
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
-    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN>,
+    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN>, dim3(grid), dim3(kSolveBlock),
-                                            args, smem, st);
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H>, dim3(grid),
+                                            dim3(kSolveBlock), args, smem, st);
 }
 
 template <class VT, class MT, int LAYOUT, int T, bool DYN>
@@ -1124,6 +1129,9 @@ int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, i
     return P ? launch_one<VT, MT, LAY, TT, D>(*P, grid, st) : max_grid_one<VT, MT, LAY, TT, D>(max_grid)
     if constexpr (SUBSET == 0) {
         if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1, false); }
+        if constexpr (sizeof(VT) == 4) {   // CSR, one lane per row, with the L2 hints
+            if (P && P->l2hint) return launch_one<VT, MT, LAY_CSR, 1, false, true>(*P, grid, st);
+        }
         BCS_CASE(LAY_CSR, 1, false);
     } else if constexpr (SUBSET == 1) {
         switch (tpr) {

@@ -662,3 +662,27 @@ def test_low_precision_first_inner_run_tracks_fp64_oracle(env, name):
         rel = np.abs(h - ref["hist"]) / ref["hist"]
         for i in range(9):
             assert rel[i] <= 16 * u * grow(i), (prec, i, rel[i])
+
+
+@pytest.mark.parametrize("big_ctas,big_systems", [(4, 3), (8, 0), (16, 1)])
+def test_batched_second_lane_for_the_largest_systems(env, big_ctas, big_systems):
+    """The largest systems of a batch solved by a second, concurrent launch with bigger clusters
+    (bcs_options::big_ctas): FP64 results bit-identical to each system's oracle solve, in both
+    lanes, on a first solve and a graph replay with new vectors."""
+    bcs, torch, orc = env
+    mats, sides, betas = W.batch_cd2d(count=24, seed=13, kmin=8, kmax=48)
+    Ms = [bcs.csr_upload(A) for A in mats]
+    refs = [orc.solve(A, W.rhs_ones(A), kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=20, max_restarts=29)
+            for A in mats]
+    bt = bcs.Batch(Ms, kind="p-BiCGSafe-rr", tol=1e-10, maxit=5000, rr_m=20, big_ctas=big_ctas,
+                   big_systems=big_systems)
+    for rep in range(2):
+        bs = [torch.from_numpy(W.rhs_ones(A)).cuda() for A in mats]
+        xs = [torch.zeros(A.n, dtype=torch.float64, device="cuda") for A in mats]
+        code, res = bt.solve(bs, xs)
+        assert code == 0
+        for x, r, ref in zip(xs, res, refs):
+            assert r["status"] == 0
+            assert r["iterations"] == ref["iterations"] and np.array_equal(x.cpu().numpy(), ref["x"])
+    with pytest.raises(bcs.BcsError):   # the second lane's clusters must be larger than the first's
+        bcs.Batch(Ms, kind="p-BiCGSafe-rr", big_ctas=2)
