@@ -100,7 +100,35 @@ int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* r
 int bcs_dist_get_history(bcs_dist d, double* out, int cap, int* len);
 int bcs_dist_get_scalars(bcs_dist d, double* out, int cap, int* len);
 
-/* Rank r's block and halo sizes and its number of CTAs (any pointer may be NULL). */
+/*
+ * One rank per process and GPU (the multi-GPU form of the same solve).  Every
+ * process calls bcs_dist_rank_create with the same matrix, nparts and bounds
+ * and its own rank, on its own device (the devices are taken to be alike: each
+ * rank uses all co-resident CTAs of its GPU).  Each rank's vectors, FP64 x,
+ * inner-product records and barrier word live in one device arena; the ranks
+ * exchange its CUDA IPC handle (bcs_dist_rank_export, BCS_DIST_HANDLE_BYTES
+ * bytes, e.g. through torch.distributed.all_gather_object) and every rank
+ * opens the others' (bcs_dist_rank_connect, handles in rank order; needs peer
+ * access between the GPUs, e.g. NVLink).  The halo values are then stored
+ * straight into the other GPUs' memory and all ranks meet at rank 0's barrier
+ * counter with system-scope release/acquire; every rank sums all ranks'
+ * records (in rank 0's arena) in the same order.  bcs_dist_solve then runs on
+ * every process at about the same time (a rank that starts more than
+ * spin_budget_ms after the others makes them return BCS_ERR_TIMEOUT; after
+ * any error, destroy and re-create the solvers on every rank); b_dev and
+ * x_dev are full-length on every process's device, and each rank writes its
+ * own rows of x.  Not measured: the machines this library was built on give
+ * every run one GPU, so only the one-rank form of this path has run.
+ */
+#define BCS_DIST_HANDLE_BYTES 64
+int bcs_dist_rank_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
+                         int nparts, const int64_t* bounds, int rank, int kind, double tol, int maxit,
+                         const bcs_options* opt, bcs_dist* out);
+int bcs_dist_rank_export(bcs_dist d, void* handle);
+int bcs_dist_rank_connect(bcs_dist d, const void* handles);
+
+/* Rank r's block and halo sizes and its number of CTAs (any pointer may be NULL;
+ * a process of the multi-GPU form knows its own rank only). */
 int bcs_dist_info(bcs_dist d, int rank, int64_t* row0, int64_t* nloc, int64_t* nleft, int64_t* nright,
                   int64_t* nsend, int* ctas);
 

@@ -32,7 +32,8 @@ EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_mat
             "bcs_get_scalars", "bcs_solver_destroy", "bcs_solve_batched", "bcs_batch_create", "bcs_batch_solve",
             "bcs_batch_destroy", "bcs_autotune", "bcs_batch_autotune", "bcs_status_string",
             "bcs_autotune_sell_sigma", "bcs_partition_rows", "bcs_halo_plan", "bcs_dist_create", "bcs_dist_solve",
-            "bcs_dist_get_history", "bcs_dist_get_scalars", "bcs_dist_info", "bcs_dist_destroy"]
+            "bcs_dist_get_history", "bcs_dist_get_scalars", "bcs_dist_info", "bcs_dist_destroy",
+            "bcs_dist_rank_create", "bcs_dist_rank_export", "bcs_dist_rank_connect"]
 
 
 class Options(ctypes.Structure):
@@ -107,6 +108,9 @@ def _load():
     L.bcs_dist_get_scalars.argtypes = [P, P, I, ctypes.POINTER(I)]
     L.bcs_dist_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
                                 ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I)]
+    L.bcs_dist_rank_create.argtypes = [I64, I64, P, P, P, I, P, I, I, D, I, ctypes.POINTER(Options), ctypes.POINTER(P)]
+    L.bcs_dist_rank_export.argtypes = [P, P]
+    L.bcs_dist_rank_connect.argtypes = [P, P]
     L.bcs_dist_destroy.argtypes = [P]
     L.bcs_dist_destroy.restype = None
     L.bcs_status_string.argtypes = [I]
@@ -560,3 +564,38 @@ class Dist:
         if getattr(self, "handle", None):
             lib.bcs_dist_destroy(self.handle)
             self.handle = None
+
+
+DIST_HANDLE_BYTES = 64
+
+
+class DistRank(Dist):
+    """One rank of a partitioned solve with one process per GPU (bcs_dist_rank_*): create on every
+    process, exchange export_handle() bytes (for example with torch.distributed.all_gather_object),
+    connect(handles in rank order), then solve() on every process with full-length b and x."""
+
+    def __init__(self, A, nparts, rank, kind="p-BiCGSafe", tol=1e-10, maxit=10000, bounds=None, **kw):
+        self.handle = None
+        self.n = int(A.n)
+        rp, ci, va = _np(A.rowptr, np.int64), _np(A.col, np.int32), _np(A.val, np.float64)
+        bd = None if bounds is None else _np(bounds, np.int64)
+        opts = options(**kw)
+        h = ctypes.c_void_p()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(lib.bcs_dist_rank_create(self.n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data if len(ci) else None,
+                                        va.ctypes.data if len(va) else None, int(nparts),
+                                        None if bd is None else bd.ctypes.data, int(rank), k, float(tol), int(maxit),
+                                        ctypes.byref(opts), ctypes.byref(h)), "bcs_dist_rank_create")
+        self.handle = h.value
+        self.nparts, self.rank = int(nparts), int(rank)
+
+    def export_handle(self):
+        buf = ctypes.create_string_buffer(DIST_HANDLE_BYTES)
+        _check(lib.bcs_dist_rank_export(self.handle, buf), "bcs_dist_rank_export")
+        return buf.raw
+
+    def connect(self, handles):
+        if len(handles) != self.nparts or any(len(h) != DIST_HANDLE_BYTES for h in handles):
+            raise ValueError("one %d-byte handle per rank" % DIST_HANDLE_BYTES)
+        blob = ctypes.create_string_buffer(b"".join(handles), DIST_HANDLE_BYTES * self.nparts)
+        _check(lib.bcs_dist_rank_connect(self.handle, blob), "bcs_dist_rank_connect")

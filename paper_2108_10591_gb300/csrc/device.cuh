@@ -26,6 +26,20 @@ __device__ __forceinline__ int ld_relaxed_int(const int* p) {
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// system scope (several GPUs meeting at one barrier through peer memory)
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_sys_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.sys.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_int_sys(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Grid-wide barrier for a cooperative (co-resident) launch.  A monotonic
 // arrival counter: barrier k completes when the counter reaches k*gridDim.
@@ -33,8 +47,13 @@ __device__ __forceinline__ int ld_relaxed_int(const int* p) {
 // made before the barrier by any CTA is visible after it.  The wait is
 // bounded: past `budget` cycles (or when another CTA has already failed) the
 // CTA records BCS_ERR_TIMEOUT and the call returns false; callers then leave
-// the kernel, so a missing CTA can never hang the GPU.
-struct GridBarrier {
+// the kernel, so a missing CTA can never hang the GPU.  SYS: the CTAs of
+// several GPUs meet at a counter in one GPU's memory (release/acquire at
+// system scope, so that their stores into each other's memory are visible
+// after the barrier); `epoch` starts at the barriers already passed on that
+// counter (it is not reset between solves).
+template <bool SYS>
+struct GridBarrierT {
     unsigned* count;
     int* err;
     unsigned nblocks;
@@ -46,13 +65,15 @@ struct GridBarrier {
         if (threadIdx.x == 0) {
             epoch += 1;
             const unsigned target = epoch * nblocks;
-            red_release_gpu_add(count, 1u);
+            if constexpr (SYS) red_release_sys_add(count, 1u);
+            else red_release_gpu_add(count, 1u);
             int ok = 1;
             const long long t0 = clock64();
-            while ((int)(ld_acquire_gpu(count) - target) < 0) {
-                if (ld_relaxed_int(err) != 0) { ok = 0; break; }
+            while ((int)((SYS ? ld_acquire_sys(count) : ld_acquire_gpu(count)) - target) < 0) {
+                if ((SYS ? ld_relaxed_int_sys(err) : ld_relaxed_int(err)) != 0) { ok = 0; break; }
                 if (clock64() - t0 > budget) {
-                    atomicCAS(err, 0, (int)BCS_ERR_TIMEOUT);
+                    if constexpr (SYS) atomicCAS_system(err, 0, (int)BCS_ERR_TIMEOUT);
+                    else atomicCAS(err, 0, (int)BCS_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
@@ -63,6 +84,7 @@ struct GridBarrier {
         return *s_flag != 0;
     }
 };
+using GridBarrier = GridBarrierT<false>;
 
 // ---- L2 eviction priority ----------------------------------------------------------
 // Streams that are not read again before L2 would have dropped them anyway

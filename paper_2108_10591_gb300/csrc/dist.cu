@@ -211,9 +211,35 @@ struct bcs_dist_s {
     double* host_out = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int hist_len = 0;
+    // one rank per process and GPU (bcs_dist_rank_create): this process holds
+    // rank `rank` only; every rank's vectors, x, records and barrier counter
+    // live in one arena per rank that the others open by CUDA IPC
+    int proc = 0, rank = 0, total_ctas = 0, connected = 0;
+    std::vector<int64_t> all_len, all_nleft;  // every rank's extended vector length and left halo
+    char* arena = nullptr;
+    std::vector<void*> opened;                // peers' arenas (IPC), nullptr for this rank
+    double* rec = nullptr;                    // rank 0's records (all ranks write and read them)
+    unsigned bar_base = 0;                    // barriers already passed on that counter
 };
 
 namespace {
+
+// Arena of one rank in process mode: NVEC extended vectors, the FP64 x, the
+// double-buffered records of every CTA of the solve, the barrier word; each
+// part 256-byte aligned.  Every rank computes every rank's layout.
+struct ArenaLayout {
+    size_t vec, x64, rec, bar, bytes;
+};
+ArenaLayout arena_layout(int64_t len, size_t vbytes, int total_ctas) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    ArenaLayout a;
+    a.vec = 0;
+    a.x64 = up((size_t)NVEC * (size_t)len * vbytes);
+    a.rec = a.x64 + up(sizeof(double) * (size_t)len);
+    a.bar = a.rec + up(sizeof(double) * 2 * (size_t)total_ctas * NSLOT * kRec);
+    a.bytes = a.bar + 256;
+    return a;
+}
 
 int dist_dispatch(const bcs_dist_s* d, const DistArgs* D, int grid, cudaStream_t st, int* mg) {
     if (!d->vt_f32) return dispatch_dist_f64(D, grid, st, mg);
@@ -229,10 +255,15 @@ void bcs_dist_destroy(bcs_dist d) {
     if (!d) return;
     cudaDeviceSynchronize();
     for (auto& r : d->ranks) {
+        if (d->proc) r.vecmem = nullptr, r.x64 = nullptr;   // parts of the arena
         void* ptrs[] = {r.rowptr, r.col, r.val64, r.valin, r.send_ptr, r.send_dst, r.tile_send, r.vecmem, r.x64};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
+    if (d->proc) d->bar = nullptr;   // rank 0's barrier word, inside an arena
+    for (void* p : d->opened)
+        if (p) cudaIpcCloseMemHandle(p);
+    if (d->arena) cudaFree(d->arena);
     void* ptrs[] = {d->dpeer, d->dparams, d->partials, d->bar, d->hist, d->scal, d->out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -243,9 +274,13 @@ void bcs_dist_destroy(bcs_dist d) {
     delete d;
 }
 
-int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
-                    int nparts, const int64_t* bounds, int kind, double tol, int maxit, const bcs_options* opt,
-                    bcs_dist* out) {
+}  // extern "C"
+
+// Both forms of the partitioned solver: every rank in one launch on this GPU
+// (proc_rank < 0), or rank proc_rank of a solve with one process per GPU.
+static int dist_build(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
+                      int nparts, const int64_t* bounds, int proc_rank, int kind, double tol, int maxit,
+                      const bcs_options* opt, bcs_dist* out) {
     if (!out) return BCS_ERR_ARG;
     *out = nullptr;
     if (n < 1 || n >= INT32_MAX || nnz < 0 || nnz >= INT32_MAX || !rowptr || (nnz > 0 && (!col || !val)) ||
@@ -287,24 +322,40 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
     d->vt_f32 = o.precision != BCS_FP64;
     d->valtype = o.precision == BCS_FP64 ? VAL_F64 : o.precision == BCS_FP32_REFINE ? VAL_F32 : VAL_BF16;
     d->vbytes = d->vt_f32 ? sizeof(float) : sizeof(double);
-    d->ranks.resize(nparts);
-    // CTAs: all co-resident ones, shared in proportion to the ranks' rows
+    d->proc = proc_rank >= 0;
+    d->rank = d->proc ? proc_rank : 0;
+    const int r_lo = d->proc ? proc_rank : 0, r_hi = d->proc ? proc_rank + 1 : nparts;   // ranks held here
+    d->ranks.resize(r_hi - r_lo);
+    for (const RankPlan& p : plans) {
+        const int64_t len = (int64_t)p.left.size() + std::max<int64_t>(p.npad, 32) + (int64_t)p.right.size();
+        d->all_len.push_back(len);
+        d->all_nleft.push_back((int64_t)p.left.size());
+    }
+    // CTAs: all co-resident ones, shared in proportion to the ranks' rows; one
+    // process per GPU: all of this GPU's (the GPUs are taken to be alike)
     int maxg = 0;
-    if (dist_dispatch(d, nullptr, 0, 0, &maxg) != 0 || maxg < nparts) {
+    if (dist_dispatch(d, nullptr, 0, 0, &maxg) != 0 || maxg < (d->proc ? 1 : nparts)) {
         bcs_dist_destroy(d);
-        return maxg > 0 && maxg < nparts ? BCS_ERR_ARG : BCS_ERR_CUDA;
+        return maxg > 0 ? BCS_ERR_ARG : BCS_ERR_CUDA;
     }
-    int given = 0;
-    for (int r = 0; r < nparts; ++r) {
-        const int64_t want = (int64_t)((double)maxg * (double)plans[r].nloc / (double)n);
-        d->ranks[r].ctas = (int)std::max<int64_t>(1, want);
-        given += d->ranks[r].ctas;
+    if (d->proc) {
+        d->ranks[0].ctas = maxg;
+        d->grid = maxg;
+        d->total_ctas = maxg * nparts;
+    } else {
+        int given = 0;
+        for (int r = 0; r < nparts; ++r) {
+            const int64_t want = (int64_t)((double)maxg * (double)plans[r].nloc / (double)n);
+            d->ranks[r].ctas = (int)std::max<int64_t>(1, want);
+            given += d->ranks[r].ctas;
+        }
+        for (int r = 0; given > maxg; r = (r + 1) % nparts)
+            if (d->ranks[r].ctas > 1) { --d->ranks[r].ctas; --given; }
+        d->grid = given;
+        d->total_ctas = given;
     }
-    for (int r = 0; given > maxg; r = (r + 1) % nparts)
-        if (d->ranks[r].ctas > 1) { --d->ranks[r].ctas; --given; }
-    d->grid = given;
-    for (int r = 0; r < nparts; ++r) {
-        const int64_t tiles = (plans[r].nloc + 31) / 32, warps = (int64_t)d->ranks[r].ctas * kSolveWarps;
+    for (int r = r_lo; r < r_hi; ++r) {
+        const int64_t tiles = (plans[r].nloc + 31) / 32, warps = (int64_t)d->ranks[r - r_lo].ctas * kSolveWarps;
         if ((tiles + warps - 1) / warps >= (1 << 16)) {  // per-lane exact partials hold < 2^16 tiles
             bcs_dist_destroy(d);
             return BCS_ERR_ARG;
@@ -320,9 +371,14 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
         if (cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) rc = BCS_ERR_CUDA;
     };
     std::vector<void*> peer((size_t)nparts * (NVEC + 1), nullptr);
-    for (int r = 0; r < nparts && !rc; ++r) {
+    const ArenaLayout lay = arena_layout(d->all_len[d->rank], d->vbytes, d->total_ctas);
+    if (d->proc) {
+        alloc((void**)&d->arena, lay.bytes);
+        if (!rc && cudaMemset(d->arena, 0, lay.bytes) != cudaSuccess) rc = BCS_ERR_CUDA;
+    }
+    for (int r = r_lo; r < r_hi && !rc; ++r) {
         const RankPlan& p = plans[r];
-        bcs_dist_s::Rank& R = d->ranks[r];
+        bcs_dist_s::Rank& R = d->ranks[r - r_lo];
         R.row0 = p.row0;
         R.nloc = p.nloc;
         R.npad = std::max<int64_t>(p.npad, 32);
@@ -350,8 +406,13 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
         alloc((void**)&R.send_ptr, sizeof(int32_t) * sp.size());
         alloc((void**)&R.send_dst, sizeof(int2) * (size_t)R.nsend);
         alloc((void**)&R.tile_send, ts.size());
-        alloc((void**)&R.vecmem, (size_t)NVEC * (size_t)R.len * d->vbytes);
-        alloc((void**)&R.x64, sizeof(double) * (size_t)R.len);
+        if (d->proc) {
+            R.vecmem = d->arena + lay.vec;
+            R.x64 = (double*)(d->arena + lay.x64);
+        } else {
+            alloc((void**)&R.vecmem, (size_t)NVEC * (size_t)R.len * d->vbytes);
+            alloc((void**)&R.x64, sizeof(double) * (size_t)R.len);
+        }
         put(R.rowptr, rp.data(), sizeof(int32_t) * rp.size());
         put(R.col, p.lcol.data(), sizeof(int32_t) * (size_t)nz);
         put(R.val64, val + k0, sizeof(double) * (size_t)nz);
@@ -369,17 +430,19 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
     }
     const size_t nrec = sizeof(double) * 2 * (size_t)d->grid * NSLOT * kRec;
     alloc((void**)&d->dpeer, sizeof(void*) * peer.size());
-    put(d->dpeer, peer.data(), sizeof(void*) * peer.size());
+    if (!d->proc) put(d->dpeer, peer.data(), sizeof(void*) * peer.size());   // process mode: at connect
     alloc((void**)&d->dparams, sizeof(KParams) * (size_t)nparts);
-    alloc((void**)&d->partials, nrec);
-    alloc((void**)&d->bar, 64);
+    if (!d->proc) {
+        alloc((void**)&d->partials, nrec);
+        alloc((void**)&d->bar, 64);
+    }
     alloc((void**)&d->hist, sizeof(double) * std::max(o.history_len, 1));
     alloc((void**)&d->scal, sizeof(double) * 4 * std::max(o.history_len, 1));
     alloc((void**)&d->out, sizeof(double) * NOUT);
     if (!rc && cudaMallocHost((void**)&d->host_out, sizeof(double) * NOUT + 64) != cudaSuccess) rc = BCS_ERR_OOM;
     if (!rc && cudaMallocHost((void**)&d->hparams, sizeof(KParams) * (size_t)nparts) != cudaSuccess) rc = BCS_ERR_OOM;
     if (!rc && (cudaEventCreate(&d->ev0) != cudaSuccess || cudaEventCreate(&d->ev1) != cudaSuccess)) rc = BCS_ERR_CUDA;
-    if (!rc && cudaMemset(d->partials, 0, nrec) != cudaSuccess) rc = BCS_ERR_CUDA;
+    if (!rc && !d->proc && cudaMemset(d->partials, 0, nrec) != cudaSuccess) rc = BCS_ERR_CUDA;
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = BCS_ERR_CUDA;
     if (rc) {
         bcs_dist_destroy(d);
@@ -389,17 +452,81 @@ int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t
     return BCS_OK;
 }
 
+extern "C" {
+
+int bcs_dist_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
+                    int nparts, const int64_t* bounds, int kind, double tol, int maxit, const bcs_options* opt,
+                    bcs_dist* out) {
+    return dist_build(n, nnz, rowptr, col, val, nparts, bounds, -1, kind, tol, maxit, opt, out);
+}
+
+int bcs_dist_rank_create(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
+                         int nparts, const int64_t* bounds, int rank, int kind, double tol, int maxit,
+                         const bcs_options* opt, bcs_dist* out) {
+    if (rank < 0 || rank >= nparts) return BCS_ERR_ARG;
+    return dist_build(n, nnz, rowptr, col, val, nparts, bounds, rank, kind, tol, maxit, opt, out);
+}
+
+int bcs_dist_rank_export(bcs_dist d, void* handle) {
+    if (!d || !d->proc || !handle) return BCS_ERR_ARG;
+    cudaIpcMemHandle_t h;
+    if (cudaIpcGetMemHandle(&h, d->arena) != cudaSuccess) return BCS_ERR_CUDA;
+    static_assert(sizeof(h) <= BCS_DIST_HANDLE_BYTES, "handle size");
+    memset(handle, 0, BCS_DIST_HANDLE_BYTES);
+    memcpy(handle, &h, sizeof(h));
+    return BCS_OK;
+}
+
+int bcs_dist_rank_connect(bcs_dist d, const void* handles) {
+    if (!d || !d->proc || !handles || d->connected) return BCS_ERR_ARG;
+    const int P = d->nranks;
+    d->opened.assign(P, nullptr);
+    std::vector<char*> base(P, nullptr);
+    for (int q = 0; q < P; ++q) {
+        if (q == d->rank) {
+            base[q] = d->arena;
+            continue;
+        }
+        cudaIpcMemHandle_t h;
+        memcpy(&h, (const char*)handles + (size_t)q * BCS_DIST_HANDLE_BYTES, sizeof(h));
+        void* p = nullptr;
+        if (cudaIpcOpenMemHandle(&p, h, cudaIpcMemLazyEnablePeerAccess) != cudaSuccess) return BCS_ERR_CUDA;
+        d->opened[q] = p;
+        base[q] = (char*)p;
+    }
+    std::vector<void*> peer((size_t)P * (NVEC + 1), nullptr);
+    for (int q = 0; q < P; ++q) {
+        const ArenaLayout lq = arena_layout(d->all_len[q], d->vbytes, d->total_ctas);
+        for (int v = 0; v < NVEC; ++v)
+            peer[(size_t)q * (NVEC + 1) + v] =
+                base[q] + lq.vec + ((size_t)v * (size_t)d->all_len[q] + (size_t)d->all_nleft[q]) * d->vbytes;
+        peer[(size_t)q * (NVEC + 1) + NVEC] = base[q] + lq.x64 + (size_t)d->all_nleft[q] * sizeof(double);
+    }
+    const ArenaLayout l0 = arena_layout(d->all_len[0], d->vbytes, d->total_ctas);
+    d->rec = (double*)(base[0] + l0.rec);
+    d->bar = (unsigned*)(base[0] + l0.bar);   // rank 0's barrier counter and error word
+    if (cudaMemcpy(d->dpeer, peer.data(), sizeof(void*) * peer.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return BCS_ERR_CUDA;
+    d->connected = 1;
+    return BCS_OK;
+}
+
 int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* res, void* stream) {
     NvtxRange nv("bcs_dist_solve");
-    if (!d || !b_dev || !x_dev) return BCS_ERR_ARG;
+    if (!d || !b_dev || !x_dev || (d->proc && !d->connected)) return BCS_ERR_ARG;
     if (!device_reachable(b_dev) || !device_reachable(x_dev)) return BCS_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    const int held = (int)d->ranks.size();   // all ranks, or this process's one
     DistArgs D;
     memset(&D, 0, sizeof(D));
     D.params = d->dparams;
-    D.nranks = d->nranks;
+    D.nranks = held;
+    D.rec_offset = d->proc ? d->rank * d->grid : 0;
+    D.rec_total = d->total_ctas;
+    D.bar_base = d->proc ? d->bar_base : 0u;
+    D.sys = d->proc;
     D.cta0[0] = 0;
-    for (int r = 0; r < d->nranks; ++r) {
+    for (int r = 0; r < held; ++r) {
         const bcs_dist_s::Rank& R = d->ranks[r];
         D.cta0[r + 1] = D.cta0[r] + R.ctas;
         KParams& P = d->hparams[r];
@@ -425,7 +552,7 @@ int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* r
         P.x64 = R.x64 + R.nleft;
         P.b64 = b_dev + R.row0;
         for (int v = 0; v < NVEC; ++v) P.vec[v] = R.vecmem + ((size_t)v * (size_t)R.len + (size_t)R.nleft) * d->vbytes;
-        P.partials = d->partials;
+        P.partials = d->proc ? d->rec : d->partials;
         P.bar = d->bar;
         P.err = (int*)(d->bar + 4);
         P.hist = d->hist;
@@ -439,9 +566,11 @@ int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* r
         P.bg = b_dev;
         P.xg = x_dev;
     }
-    if (cudaMemcpyAsync(d->dparams, d->hparams, sizeof(KParams) * (size_t)d->nranks, cudaMemcpyHostToDevice, st) !=
+    // process mode: the shared counter is not reset (every rank would race the
+    // others' first arrivals); each rank adds the barriers it passed instead
+    if (cudaMemcpyAsync(d->dparams, d->hparams, sizeof(KParams) * (size_t)held, cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
-        cudaMemsetAsync(d->bar, 0, 64, st) != cudaSuccess ||
+        (!d->proc && cudaMemsetAsync(d->bar, 0, 64, st) != cudaSuccess) ||
         cudaMemsetAsync(d->out, 0, sizeof(double) * NOUT, st) != cudaSuccess)
         return BCS_ERR_CUDA;
     cudaEventRecord(d->ev0, st);
@@ -457,6 +586,7 @@ int bcs_dist_solve(bcs_dist d, const double* b_dev, double* x_dev, bcs_result* r
     const double* o = d->host_out;
     const int status = herr ? herr : (int)o[O_STATUS];
     d->hist_len = (int)o[O_HISTLEN];
+    if (d->proc) d->bar_base += (unsigned)o[O_SYNCS];
     if (res) {
         memset(res, 0, sizeof(*res));
         res->status = status;
@@ -501,7 +631,9 @@ int bcs_dist_get_scalars(bcs_dist d, double* out, int cap, int* len) {
 int bcs_dist_info(bcs_dist d, int rank, int64_t* row0, int64_t* nloc, int64_t* nleft, int64_t* nright,
                   int64_t* nsend, int* ctas) {
     if (!d || rank < 0 || rank >= d->nranks) return BCS_ERR_ARG;
-    const bcs_dist_s::Rank& R = d->ranks[rank];
+    const int idx = d->proc ? (rank == d->rank ? 0 : -1) : rank;   // a process holds its own rank only
+    if (idx < 0) return BCS_ERR_ARG;
+    const bcs_dist_s::Rank& R = d->ranks[idx];
     if (row0) *row0 = R.row0;
     if (nloc) *nloc = R.nloc;
     if (nleft) *nleft = R.nleft;

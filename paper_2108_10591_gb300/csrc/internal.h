@@ -102,6 +102,12 @@ struct DistArgs {
     const KParams* params;
     int cta0[kDistMaxRanks + 1];
     int nranks;
+    // records and barrier: this launch's CTAs are rec_offset .. rec_offset +
+    // gridDim - 1 of rec_total (one launch per GPU: rank * CTAs per rank, of
+    // ranks * CTAs per rank); the barrier counter has passed bar_base barriers
+    int rec_offset, rec_total;
+    unsigned bar_base;
+    int sys;   // the ranks are on several GPUs: system-scope barrier
 };
 
 // Batched solves: the systems' parameter blocks (without workspace), their

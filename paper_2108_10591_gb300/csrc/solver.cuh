@@ -185,8 +185,9 @@ __device__ __forceinline__ void reduce_partials(const unsigned long long* base, 
 // rank/size: the CTA's place among all CTAs that write inner-product records
 // and meet at the barriers; trank/tsize (when >= 0): its place among the CTAs
 // that share the tiles of one row block (a rank of a partitioned solve).
-struct GridGroup {
-    GridBarrier gb;
+template <bool SYS>
+struct GridGroupT {
+    GridBarrierT<SYS> gb;
     int rank, size;
     int nsync = 0;   // grid barriers passed (reported with the result)
     int trank = -1, tsize = -1;
@@ -197,6 +198,7 @@ struct GridGroup {
         return gb.sync(flag);
     }
 };
+using GridGroup = GridGroupT<false>;
 struct ClusterGroup {
     int rank, size;
     int nsync = 0;
@@ -234,6 +236,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     const int64_t n = P.n, ntiles = P.ntiles;
     const int nblk = grp.size;
     const int rank = grp.rank;
+    // the CTA that writes the result block and the history: CTA 0, or in a
+    // partitioned solve the first CTA of every rank (each rank's process keeps
+    // its own copy; ranks of one launch write the same values)
+    const bool writer = DIST ? grp.tile_rank() == 0 : rank == 0;
     const int kind = P.kind;
     const bool mixed = P.mixed != 0;
     // with enough warps the grid reduction leaves warp 0 (the scalar recurrence)
@@ -418,7 +424,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     int status = BCS_NOT_CONVERGED, inner_status = BCS_OK;
     int n_spmv = 0, n_red = 0;  // passes over the matrix and grid reductions (reported with the result)
     const unsigned long long t_start = global_ns();
-    grp.nsync = 0;
+    // barriers reported with the result: from here on; a partitioned solve
+    // counts every barrier of the launch (its prologue's too), since the
+    // one-process-per-GPU form continues the shared counter from that count
+    if constexpr (!DIST) grp.nsync = 0;
     int total = 0, evals = 0, runs = 0, hist_len = 0, rr_steps = 0, fallbacks = 0;
     double r0n = 0.0, thresh = 0.0, r0ref = 1.0, rtrue = 0.0, last_rec = 0.0;
     double alpha_p = 0.0, zeta_p = 0.0, f_p = 0.0;  // thread 0 of each CTA
@@ -651,7 +660,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     dec = 1;
                     st = BCS_ERR_BREAKDOWN;
                 } else {
-                    if (rank == 0) {
+                    if (writer) {
                         if (hist_len < P.hist_cap) P.hist[hist_len] = rn / r0ref;
                         if (runs == 1 && i < P.hist_cap) {
                             P.scal[4 * i + 0] = alpha; P.scal[4 * i + 1] = beta;
@@ -1007,7 +1016,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
         if (!grp.sync(&s_flag)) { stg.settle(); return; }
     }
 
-    if (rank == 0 && threadIdx.x == 0) {
+    if (writer && threadIdx.x == 0) {
         P.out[O_STATUS] = status;
         P.out[O_ITERS] = total;
         P.out[O_OUTER] = runs;
@@ -1046,7 +1055,7 @@ __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_cons
 // Partitioned solve (bcs_dist.h): one cooperative launch whose CTAs are split
 // into ranks; each CTA runs the solver body on its rank's row block, all CTAs
 // meet at the one grid barrier and sum every rank's inner-product records.
-template <class VT, class MT>
+template <class VT, class MT, bool SYS>
 __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel_dist(const __grid_constant__ DistArgs D) {
     __shared__ KParams sP;
     __shared__ int s_r;
@@ -1058,10 +1067,14 @@ __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel_dist(const __grid
     }
     __syncthreads();
     const int r = s_r;
-    GridGroup grp{GridBarrier{sP.bar, sP.err, gridDim.x, 0u, sP.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
+    // records and barrier: this launch's CTAs are rec_offset .. of rec_total
+    // (the CTAs of every process of the solve; all of them when one launch
+    // holds every rank)
+    GridGroupT<SYS> grp{GridBarrierT<SYS>{sP.bar, sP.err, (unsigned)D.rec_total, D.bar_base, sP.spin_budget},
+                        D.rec_offset + (int)blockIdx.x, D.rec_total};
     grp.trank = (int)blockIdx.x - D.cta0[r];
     grp.tsize = D.cta0[r + 1] - D.cta0[r];
-    solve_body<VT, MT, LAY_CSR, 1, kSolveWarps, false, GridGroup, true>(sP, grp);
+    solve_body<VT, MT, LAY_CSR, 1, kSolveWarps, false, GridGroupT<SYS>, true>(sP, grp);
 }
 
 // dynamic shared memory of the solver kernels: the per-warp staging buffers
@@ -1101,21 +1114,21 @@ int max_grid_one(int* grid) {
 template <class VT, class MT>
 int dispatch_dist(const DistArgs* D, int grid, cudaStream_t st, int* max_grid) {
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
-    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel_dist<VT, MT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fn = (D && D->sys) ? (const void*)solve_kernel_dist<VT, MT, true>
+                                   : (const void*)solve_kernel_dist<VT, MT, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     if (!D) {
         int dev = 0, sms = 0, per = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel_dist<VT, MT>, kSolveBlock, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel_dist<VT, MT, false>, kSolveBlock, smem);
         *max_grid = sms * per;
         return (int)e;
     }
     void* args[] = {(void*)D};
-    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel_dist<VT, MT>, dim3(grid), dim3(kSolveBlock), args,
-                                            smem, st);
+    return (int)cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSolveBlock), args, smem, st);
 }
 
 // Dispatch over layout and lanes-per-row for one (VT, MT) pair; each

@@ -127,3 +127,31 @@ def test_dist_cd3d_128_matches_oracle_full_solve(env, nparts):
     assert res["status"] == 0
     assert res["iterations"] == g["iterations"] and res["outer_steps"] == g["outer_steps"]
     assert hashlib.sha256(np.ascontiguousarray(x, dtype="<f8").tobytes()).hexdigest() == g["x_sha256"]
+
+
+def test_one_process_per_gpu_form_with_one_rank(env):
+    """The multi-GPU form (bcs_dist_rank_*: one process per GPU, peers' arenas opened by CUDA IPC,
+    a system-scope barrier on rank 0's counter that is not reset between solves) with the one
+    rank this machine allows: export, connect, two solves in a row, each bit-identical to the
+    oracle; a solve before connect and a rank outside the partition are refused."""
+    bcs, torch, orc = env
+    A = W.cd2d(48, 10.0)
+    b = W.rhs_ones(A)
+    ref = orc.solve(A, b, kind="p-BiCGSafe", tol=1e-10, maxit=2000, max_restarts=29)
+    D = bcs.DistRank(A, 1, 0, kind="p-BiCGSafe", tol=1e-10, maxit=2000)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    with pytest.raises(bcs.BcsError):
+        D.solve(bd, x)
+    h = D.export_handle()
+    assert len(h) == bcs.DIST_HANDLE_BYTES
+    D.connect([h])
+    for _ in range(2):
+        x.zero_()
+        res = D.solve(bd, x)
+        assert res["status"] == 0 and res["iterations"] == ref["iterations"]
+        assert np.array_equal(x.cpu().numpy(), ref["x"])
+        assert np.array_equal(D.history(), ref["hist"])
+    assert D.info(0)["nloc"] == A.n
+    with pytest.raises(bcs.BcsError):
+        bcs.DistRank(A, 2, 2)
