@@ -81,6 +81,13 @@ def lib(parallel=False):
         L.orc_solve_hooked.argtypes = [ctypes.c_int64, P, P, ctypes.POINTER(_Opts), _MV_FN, _DOT_FN, P, P,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(_Result)]
         L.orc_solve_hooked.restype = ctypes.c_int
+        L.orc_bjacobi_blocks.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, P, P]
+        L.orc_bjacobi_blocks.restype = ctypes.c_int
+        L.orc_bjacobi_apply.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P]
+        L.orc_bjacobi_apply.restype = None
+        L.orc_solve_bjacobi.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, P, P, ctypes.POINTER(_Opts),
+                                        P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(_Result)]
+        L.orc_solve_bjacobi.restype = ctypes.c_int
         _LIBS[parallel] = L
     return _LIBS[parallel]
 
@@ -242,3 +249,53 @@ def solve_hooked(n_local, b, mv, dot, x0=None, kind="p-BiCGSafe", tol=1e-10, max
     return dict(x=x, hist=hist[:hl.value].copy(), status=st, status_name=STATUS.get(st, str(st)),
                 iterations=res.iterations, restarts=res.restarts, rr_steps=res.rr_steps,
                 rel_res_true=res.rel_res_true, scalars=scal[:4 * k].reshape(-1, 4).copy())
+
+
+def bjacobi_blocks(A, bs):
+    """Diagonal blocks D of A (bs consecutive rows each, the last block ragged) and their inverses
+    E by Gauss-Jordan with partial pivoting, as [n, bs] arrays: row i holds its block row's
+    entries in the block's columns (zero beyond the block).  Raises ValueError for a singular
+    block."""
+    rp, ci, va = _csr(A)
+    n = A.n
+    D = np.zeros((max(n, 1), bs))
+    E = np.zeros((max(n, 1), bs))
+    st = lib().orc_bjacobi_blocks(n, _p(rp), _p(ci), _p(va), int(bs), _p(D), _p(E))
+    if st != 0:
+        raise ValueError("singular diagonal block (or bad block size)")
+    return D[:n], E[:n]
+
+
+def bjacobi_apply(M, v, bs):
+    """z = M v block by block (M = D or E from bjacobi_blocks)."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    z = np.zeros(len(v))
+    lib().orc_bjacobi_apply(len(v), int(bs), _p(M), _p(v), _p(z))
+    return z
+
+
+def solve_bjacobi(A, b, bs, x0=None, kind="p-BiCGSafe", tol=1e-10, maxit=10000, rr_m=100, rr_M=None,
+                  max_restarts=0, hist_cap=None):
+    """Algorithm 3/4/5 with block-Jacobi right preconditioning (see orc_solve_bjacobi): the runs
+    on A M^-1 from y_0 = M x_0, x = M^-1 y.  Returns the same dict as solve() without the state
+    dump."""
+    rp, ci, va = _csr(A)
+    n = A.n
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    o = _Opts(KINDS[kind] if isinstance(kind, str) else int(kind), tol, maxit, rr_m,
+              maxit + 1 if rr_M is None else rr_M, max_restarts, -1, 0)
+    cap = (maxit + 1) * (max_restarts + 1) + 4 if hist_cap is None else hist_cap
+    hist = np.zeros(cap)
+    scal = np.zeros(4 * cap)
+    hl = ctypes.c_int(0)
+    res = _Result()
+    st = lib().orc_solve_bjacobi(n, _p(rp), _p(ci), _p(va), int(bs), _p(b), _p(x), ctypes.byref(o), _p(hist), cap,
+                                 ctypes.byref(hl), _p(scal), ctypes.byref(res))
+    k = min(res.iterations + 1, cap)
+    return dict(x=x, hist=hist[:hl.value].copy(), status=st, status_name=STATUS.get(st, str(st)),
+                iterations=res.iterations, restarts=res.restarts, fallbacks=res.fallbacks,
+                rr_steps=res.rr_steps, rel_res_recursive=res.rel_res_recursive,
+                rel_res_true=res.rel_res_true, r0_norm=res.r0_norm,
+                scalars=scal[:4 * k].reshape(-1, 4).copy())

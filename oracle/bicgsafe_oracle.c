@@ -28,6 +28,9 @@
  *   R8  shadow residual r0* = r_0.
  *   R9  in Alg. 5 the replacement sets l_i = A t_i.
  *   R10 residual replacement at i mod m == 0, 0 < i < M.
+ *   R17 (build addition) block-Jacobi right preconditioning (orc_solve_bjacobi):
+ *       the runs above on A M^-1 with M = the diagonal blocks of A, from
+ *       y_0 = M x_0, returning x = M^-1 y (see the block-Jacobi section).
  *   R14 (build addition) at recursive convergence the FP64 true residual
  *       ||b - A x|| is computed; if it exceeds eps*||r_0|| of the first run, the
  *       method restarts from x (new r_0 = b - A x, r0* = r_0, auxiliaries
@@ -680,4 +683,140 @@ void orc_to_bf16(int64_t n, const double* in, uint16_t* out)
         if (rounded >= ldexp(1.0, 128)) fb = 0x7F800000u; /* overflow to infinity */
         out[i] = (uint16_t)(sign | (uint16_t)((fb >> 16) & 0x7FFFu));
     }
+}
+
+/* ---- block-Jacobi preconditioning (build addition: the paper, Section 5,
+ *      uses no preconditioner) ------------------------------------------- */
+
+/*
+ * Right preconditioning with M = the block diagonal of A in blocks of bs
+ * consecutive rows (the last block holds the remaining rows).  The runs
+ * solve (A M^-1) y = b from y_0 = M x_0 and return x = M^-1 y; the residual
+ * b - (A M^-1) y of the solved system is b - A x, so the tolerance keeps
+ * its meaning.
+ *
+ * Storage: for row i of the block that starts at row b0 and holds m rows, the
+ * row's m entries of the block D = A[b0..b0+m, b0..b0+m] and of its inverse
+ * E = D^-1 are at i*bs + j, j = 0..m-1 (zero for j >= m).
+ *
+ * E is computed by Gauss-Jordan elimination on [D | I]: for each pivot column
+ * p in order, the pivot is the first row r >= p with the largest |a[r][p]|;
+ * that row is swapped into place, divided by the pivot (every entry, the
+ * pivot itself included, by the saved pivot value), and for every other row
+ * r the multiple f = a[r][p] of it is subtracted as a[r][c] - f * a[p][c]
+ * (product and difference rounded separately).  A zero, NaN or infinite
+ * pivot makes the block singular: ORC_ERR_ARG.  A repeated (row, column)
+ * entry of A keeps its last value in D.
+ */
+int orc_bjacobi_blocks(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int bs,
+                       double* D, double* E)
+{
+    if (n < 0 || bs < 1 || bs > 32) return ORC_ERR_ARG;
+    double a[32 * 32], inv[32 * 32];
+    for (int64_t b0 = 0; b0 < n; b0 += bs) {
+        const int m = (int)((n - b0) < bs ? (n - b0) : bs);
+        for (int k = 0; k < m * m; ++k) { a[k] = 0.0; inv[k] = 0.0; }
+        for (int r = 0; r < m; ++r) {
+            for (int64_t k = rowptr[b0 + r]; k < rowptr[b0 + r + 1]; ++k) {
+                const int64_t c = (int64_t)col[k] - b0;
+                if (c >= 0 && c < m) a[r * m + c] = val[k];
+            }
+            inv[r * m + r] = 1.0;
+        }
+        for (int r = 0; r < m; ++r)
+            for (int j = 0; j < bs; ++j) D[(b0 + r) * bs + j] = j < m ? a[r * m + j] : 0.0;
+        for (int p = 0; p < m; ++p) {
+            int piv = p;
+            double big = fabs(a[p * m + p]);
+            for (int r = p + 1; r < m; ++r)
+                if (fabs(a[r * m + p]) > big) { big = fabs(a[r * m + p]); piv = r; }
+            if (!(big > 0.0) || !finite(big)) return ORC_ERR_ARG;
+            if (piv != p) {
+                for (int c = 0; c < m; ++c) {
+                    double t = a[p * m + c]; a[p * m + c] = a[piv * m + c]; a[piv * m + c] = t;
+                    t = inv[p * m + c]; inv[p * m + c] = inv[piv * m + c]; inv[piv * m + c] = t;
+                }
+            }
+            const double d = a[p * m + p];
+            for (int c = 0; c < m; ++c) {
+                a[p * m + c] = a[p * m + c] / d;
+                inv[p * m + c] = inv[p * m + c] / d;
+            }
+            for (int r = 0; r < m; ++r) {
+                if (r == p) continue;
+                const double f = a[r * m + p];
+                for (int c = 0; c < m; ++c) {
+                    a[r * m + c] = a[r * m + c] - f * a[p * m + c];
+                    inv[r * m + c] = inv[r * m + c] - f * inv[p * m + c];
+                }
+            }
+        }
+        for (int r = 0; r < m; ++r)
+            for (int j = 0; j < bs; ++j) E[(b0 + r) * bs + j] = j < m ? inv[r * m + j] : 0.0;
+    }
+    return ORC_OK;
+}
+
+/* z = M v block by block (M = D or E as stored by orc_bjacobi_blocks):
+ * z_i = sum over the block's columns j of M[i][j] v[b0 + j], accumulated with
+ * fma in column order starting from zero.  z must not overlap v. */
+void orc_bjacobi_apply(int64_t n, int bs, const double* M, const double* v, double* z)
+{
+    ORC_ROWS
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t b0 = i - i % bs;
+        const int m = (int)((n - b0) < bs ? (n - b0) : bs);
+        double acc = 0.0;
+        for (int j = 0; j < m; ++j) acc = fma(M[i * bs + j], v[b0 + j], acc);
+        z[i] = acc;
+    }
+}
+
+typedef struct {
+    int64_t n;
+    const int64_t* rowptr; const int32_t* col; const double* val;
+    int bs;
+    const double* E;
+    double* z;
+} orc_bj_ctx;
+
+/* y = (A M^-1) x: z = E x block by block, then y = A z */
+static void mv_bjacobi(void* ctx, const double* x, double* y)
+{
+    orc_bj_ctx* c = (orc_bj_ctx*)ctx;
+    orc_bjacobi_apply(c->n, c->bs, c->E, x, c->z);
+    orc_spmv(c->n, c->rowptr, c->col, c->val, c->z, y);
+}
+static double dot_bjacobi(void* ctx, const double* x, const double* y)
+{
+    return orc_dot(((const orc_bj_ctx*)ctx)->n, x, y);
+}
+
+int orc_solve_bjacobi(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int bs,
+                      const double* b, double* x, const orc_opts* o,
+                      double* hist, int hist_cap, int* hist_len, double* scal_hist, orc_result* res)
+{
+    memset(res, 0, sizeof(*res));
+    if (hist_len) *hist_len = 0;
+    if (n < 0 || bs < 1 || bs > 32) { res->status = ORC_ERR_ARG; return ORC_ERR_ARG; }
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    double* D = (double*)calloc(nn * (size_t)bs, sizeof(double));
+    double* E = (double*)calloc(nn * (size_t)bs, sizeof(double));
+    double* y = (double*)calloc(nn, sizeof(double));
+    double* z = (double*)calloc(nn, sizeof(double));
+    int st = orc_bjacobi_blocks(n, rowptr, col, val, bs, D, E);
+    if (st != ORC_OK) {
+        res->status = st;
+    } else {
+        orc_bjacobi_apply(n, bs, D, x, y);            /* y_0 = M x_0 */
+        orc_bj_ctx c = {n, rowptr, col, val, bs, E, z};
+        orc_ws w;
+        memset(&w, 0, sizeof(w));
+        w.n = n; w.b = b;
+        w.mv = mv_bjacobi; w.dot = dot_bjacobi; w.ctx = &c;
+        st = solve_runs(&w, y, o, hist, hist_cap, hist_len, scal_hist, NULL, NULL, res);
+        orc_bjacobi_apply(n, bs, E, y, x);            /* x = M^-1 y */
+    }
+    free(D); free(E); free(y); free(z);
+    return st;
 }
