@@ -60,8 +60,20 @@ enum { BCS_LAYOUT_AUTO = 0, BCS_LAYOUT_CSR = 1, BCS_LAYOUT_SELL = 2 };
  * bcs_solver_create) and returns x = D^-1 y; x0 enters as y0 = D x0.  The
  * residual of the solved system equals b - A x, so tol keeps its meaning.
  * Requires every diagonal entry stored, nonzero and finite (else
- * BCS_ERR_ARG at bcs_solver_create). */
-enum { BCS_PRECOND_NONE = 0, BCS_PRECOND_JACOBI = 1 };
+ * BCS_ERR_ARG at bcs_solver_create).
+ * BCS_PRECOND_BLOCK_JACOBI: right preconditioning with M = the diagonal blocks
+ * of A, bcs_options.block_size consecutive rows each (the last block holds the
+ * remaining rows): the solver runs on (A M^-1) y = b from y0 = M x0 and returns
+ * x = M^-1 y.  The inverse blocks are formed at bcs_solver_create by
+ * Gauss-Jordan elimination with partial pivoting (BCS_ERR_ARG for a singular
+ * block).  M^-1 is not folded into the matrix: every vector that the solver
+ * multiplies by A is also written as M^-1 v by the same pass that writes v
+ * (the blocks lie inside the solver's 32-row tiles, so this needs no extra
+ * barrier), and the products gather that copy.  Single-system solves with
+ * CSR, one lane per row and the static tile order (the defaults are adjusted;
+ * an explicit other choice is BCS_ERR_ARG), kinds BCS_SSBICGSAFE2 and
+ * BCS_P_BICGSAFE. */
+enum { BCS_PRECOND_NONE = 0, BCS_PRECOND_JACOBI = 1, BCS_PRECOND_BLOCK_JACOBI = 2 };
 
 /* Value copies held on the device (bit mask; FP64 is always kept). */
 enum { BCS_STORE_F64 = 1, BCS_STORE_F32 = 2, BCS_STORE_BF16 = 4 };
@@ -103,7 +115,8 @@ typedef struct {
     int tile_order;       /* single system: 0 = library choice, 1 = static (tile t to warp t mod warps),
                              2 = dynamic (warps claim tiles from a counter); FP64 results do not depend on
                              it, refinement-mode results may in the last bits */
-    int precond;          /* BCS_PRECOND_NONE (default) or BCS_PRECOND_JACOBI (single-system solves) */
+    int precond;          /* BCS_PRECOND_NONE (default), BCS_PRECOND_JACOBI or BCS_PRECOND_BLOCK_JACOBI
+                             (single-system solves) */
     int big_ctas;         /* batched solves: 0 (default) = one lane; 2, 4, 8 or 16 = the largest systems
                              are solved concurrently by a second persistent launch whose clusters have
                              this many CTAs (larger than ctas_per_sm), so that the longest solves do not
@@ -111,6 +124,8 @@ typedef struct {
     int big_systems;      /* batched solves with big_ctas: how many of the largest systems (by nnz + n)
                              take the second lane, one cluster each; 0 = as many clusters of big_ctas as
                              fit in a quarter of the device */
+    int block_size;       /* BCS_PRECOND_BLOCK_JACOBI: rows per diagonal block, 1, 2, 4, 8, 16 or 32
+                             (0 = the default, 8) */
 } bcs_options;
 
 typedef struct {
@@ -276,6 +291,18 @@ int bcs_solve_host(bcs_solver s, const double* b_host, double* x_host, bcs_resul
  */
 int bcs_get_history(bcs_solver s, double* out, int cap, int* len);
 int bcs_get_scalars(bcs_solver s, double* out, int cap, int* len);
+
+/*
+ * Block-Jacobi solvers (BCS_PRECOND_BLOCK_JACOBI): copy the diagonal blocks D
+ * and their inverses E to host buffers of n * block_size doubles each (either
+ * may be NULL).  Row i of the block that starts at row b0 and holds m rows
+ * stores its m entries in the block's columns b0 .. b0+m-1 at
+ * i * block_size + j, j < m, and zero for j >= m.  *bs receives block_size
+ * (may be NULL).  BCS_ERR_ARG for a solver without block-Jacobi
+ * preconditioning.  Synchronous (waits for the device).  No counterpart in the
+ * paper (a build addition, like the preconditioner itself).
+ */
+int bcs_solver_precond_blocks(bcs_solver s, double* D, double* E, int* bs);
 
 /* Free a solver (NULL is ignored).  Waits for the device first (a solve still
  * in flight on any stream finishes before its workspace is released). */

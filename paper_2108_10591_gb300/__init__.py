@@ -33,7 +33,7 @@ EXPORTED = ["bcs_options_default", "bcs_csr_upload", "bcs_matrix_info", "bcs_mat
             "bcs_batch_destroy", "bcs_autotune", "bcs_batch_autotune", "bcs_status_string",
             "bcs_autotune_sell_sigma", "bcs_partition_rows", "bcs_halo_plan", "bcs_dist_create", "bcs_dist_solve",
             "bcs_dist_get_history", "bcs_dist_get_scalars", "bcs_dist_info", "bcs_dist_destroy",
-            "bcs_dist_rank_create", "bcs_dist_rank_export", "bcs_dist_rank_connect"]
+            "bcs_dist_rank_create", "bcs_dist_rank_export", "bcs_dist_rank_connect", "bcs_solver_precond_blocks"]
 
 
 class Options(ctypes.Structure):
@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("layout", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("max_ctas", ctypes.c_int), ("spin_budget_ms", ctypes.c_double), ("inner_maxit", ctypes.c_int),
                 ("inner_stall", ctypes.c_int), ("tile_order", ctypes.c_int), ("precond", ctypes.c_int),
-                ("big_ctas", ctypes.c_int), ("big_systems", ctypes.c_int)]
+                ("big_ctas", ctypes.c_int), ("big_systems", ctypes.c_int), ("block_size", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -88,6 +88,7 @@ def _load():
     L.bcs_solve_host.argtypes = [P, P, P, ctypes.POINTER(Result), P]
     L.bcs_get_history.argtypes = [P, P, I, ctypes.POINTER(I)]
     L.bcs_get_scalars.argtypes = [P, P, I, ctypes.POINTER(I)]
+    L.bcs_solver_precond_blocks.argtypes = [P, P, P, ctypes.POINTER(I)]
     L.bcs_solver_destroy.argtypes = [P]
     L.bcs_solver_destroy.restype = None
     L.bcs_solve_batched.argtypes = [I, P, I, D, I, ctypes.POINTER(Options), P, P, P, P]
@@ -196,7 +197,7 @@ def options(**kw):
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
         if k == "precond" and isinstance(v, str):
-            v = {"none": 0, "jacobi": 1}[v]
+            v = {"none": 0, "jacobi": 1, "block-jacobi": 2}[v]
         if k == "layout" and isinstance(v, str):
             v = {"auto": LAYOUT_AUTO, "csr": LAYOUT_CSR, "sell": LAYOUT_SELL}[v]
         setattr(o, k, v)
@@ -364,6 +365,18 @@ def get_scalars(S):
     out = np.zeros(4 * max(ln.value, 1))
     _check(lib.bcs_get_scalars(S.handle, out.ctypes.data, ln.value, ctypes.byref(ln)), "bcs_get_scalars")
     return out[:4 * ln.value].reshape(-1, 4)
+
+
+def precond_blocks(S):
+    """bcs_solver_precond_blocks: the diagonal blocks D and their inverses E of a block-Jacobi
+    solver as [n, block_size] numpy arrays (row i: its entries in its block's columns)."""
+    bs = ctypes.c_int()
+    _check(lib.bcs_solver_precond_blocks(S.handle, None, None, ctypes.byref(bs)), "bcs_solver_precond_blocks")
+    n = S.M.n
+    D = np.zeros((max(n, 1), bs.value))
+    E = np.zeros((max(n, 1), bs.value))
+    _check(lib.bcs_solver_precond_blocks(S.handle, D.ctypes.data, E.ctypes.data, None), "bcs_solver_precond_blocks")
+    return D[:n], E[:n]
 
 
 def solve_batched(Ms, bs, xs, kind="p-BiCGSafe", tol=1e-10, maxit=10000, stream=None, **kw):

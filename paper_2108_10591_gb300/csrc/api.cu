@@ -16,7 +16,8 @@ namespace bcs {
 #define BCS_DECL(tag)                                                                                  \
     int dispatch_##tag##_0(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid); \
     int dispatch_##tag##_1(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid); \
-    int dispatch_##tag##_2(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
+    int dispatch_##tag##_2(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid); \
+    int dispatch_##tag##_3(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid);
 BCS_DECL(f64)
 BCS_DECL(f32)
 BCS_DECL(bf16)
@@ -27,6 +28,8 @@ int dispatch_batched_bf16(const BatchArgs* B, int tpr, int nclusters, cudaStream
 int default_tpr(const bcs_matrix_s* A, int precision);
 int precond_setup(bcs_solver s);
 int precond_scale(bcs_solver s, double* x, int into, cudaStream_t st);
+int bjacobi_setup(bcs_solver s);
+int bjacobi_apply(bcs_solver s, double* x, int inverse, cudaStream_t st);
 }  // namespace bcs
 
 namespace {
@@ -35,7 +38,11 @@ namespace {
 bool dyn_supported(int layout, int tpr) { return layout == LAY_SELL || tpr == 1 || tpr == 8 || tpr == -1; }
 
 int dispatch(const KParams* P, int vt_f32, int valtype, int layout, int tpr, int dyn, int grid, cudaStream_t st,
-             int* mg) {
+             int* mg, int bj = 0) {
+    if (bj) {   // block-Jacobi: CSR, one lane per row, static order
+        if (!vt_f32) return dispatch_f64_3(P, layout, tpr, grid, st, mg);
+        return valtype == VAL_F32 ? dispatch_f32_3(P, layout, tpr, grid, st, mg) : dispatch_bf16_3(P, layout, tpr, grid, st, mg);
+    }
     const int sub = (dyn && dyn_supported(layout, tpr)) ? 2 : (layout == LAY_SELL || tpr == 1) ? 0 : 1;
     if (!vt_f32)
         return sub == 2 ? dispatch_f64_2(P, layout, tpr, grid, st, mg)
@@ -95,7 +102,10 @@ int check_options(const bcs_options& o) {
     if (!(o.spin_budget_ms > 0.0)) return BCS_ERR_ARG;
     if (o.inner_maxit < 0 || o.inner_stall < 0) return BCS_ERR_ARG;
     if (o.tile_order < 0 || o.tile_order > 2) return BCS_ERR_ARG;
-    if (o.precond != BCS_PRECOND_NONE && o.precond != BCS_PRECOND_JACOBI) return BCS_ERR_ARG;
+    if (o.precond != BCS_PRECOND_NONE && o.precond != BCS_PRECOND_JACOBI && o.precond != BCS_PRECOND_BLOCK_JACOBI)
+        return BCS_ERR_ARG;
+    if (o.block_size != 0 && (o.block_size < 1 || o.block_size > 32 || (o.block_size & (o.block_size - 1))))
+        return BCS_ERR_ARG;
     if (o.big_ctas != 0 && o.big_ctas != 2 && o.big_ctas != 4 && o.big_ctas != 8 && o.big_ctas != 16) return BCS_ERR_ARG;
     if (o.big_systems < 0) return BCS_ERR_ARG;
     return BCS_OK;
@@ -167,7 +177,7 @@ void bcs_solver_destroy(bcs_solver s) {
     if (!s) return;
     cudaDeviceSynchronize();
     void* ptrs[] = {s->vecmem, s->x64w, s->b64w, s->partials, s->bar, s->hist, s->scal, s->out, s->xb_dev,
-                    s->pdiag, s->pval64, s->pvalin};
+                    s->pdiag, s->pval64, s->pvalin, s->bjD, s->bjE, s->bjE32, s->bjhat, s->bjxh};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->host_out) cudaFreeHost(s->host_out);
@@ -190,6 +200,15 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
         o.layout = (tl && (A->layouts & tl)) ? tl : BCS_LAYOUT_CSR;
     }
     if (!(A->layouts & o.layout)) return BCS_ERR_ARG;
+    const bool bj = o.precond == BCS_PRECOND_BLOCK_JACOBI;
+    if (bj) {
+        // built for CSR with one lane per row in the static tile order, and for
+        // the kinds whose products are all in the fused phases
+        if (o.layout != BCS_LAYOUT_CSR || (o.threads_per_row != 0 && o.threads_per_row != 1) || o.tile_order == 2 ||
+            kind == BCS_P_BICGSAFE_RR)
+            return BCS_ERR_ARG;
+        if (o.block_size == 0) o.block_size = 8;
+    }
     bcs_solver s = new bcs_solver_s();
     s->A = A;
     s->kind = kind;
@@ -200,6 +219,7 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (rc) { delete s; return rc; }
     s->layout = o.layout == BCS_LAYOUT_SELL ? LAY_SELL : LAY_CSR;
     s->tpr = s->layout == LAY_SELL ? 1 : (o.threads_per_row ? o.threads_per_row : default_tpr(A, o.precision));
+    if (bj) s->tpr = 1;
     s->vbytes = s->vt_f32 ? sizeof(float) : sizeof(double);
     const int64_t n = A->n, nn = std::max<int64_t>(n, 1);
     const int64_t ntiles = (n + 31) / 32;
@@ -208,7 +228,9 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     // share of tiles then varies too much for a static split), else static
     const bool irregular = (double)A->max_row > 4.0 * A->avg_row + 4.0;
     s->dyn = ((o.tile_order == 2 || (o.tile_order == 0 && irregular)) && dyn_supported(s->layout, s->tpr)) ? 1 : 0;
-    if (dispatch(nullptr, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, 0, 0, &maxg) != 0 || maxg <= 0) {
+    if (bj) s->dyn = 0;
+    s->bj_bs = bj ? o.block_size : 0;
+    if (dispatch(nullptr, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, 0, 0, &maxg, bj) != 0 || maxg <= 0) {
         delete s;
         return BCS_ERR_CUDA;
     }
@@ -233,7 +255,7 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     // vectors padded to whole 32-row tiles: the staging copies move full tiles
     const int64_t npad = ((n + 31) / 32) * 32 > 0 ? ((n + 31) / 32) * 32 : 32;
     // the hinted kernels exist for CSR with one lane per row and the static tile order
-    s->l2hint = (s->layout == LAY_CSR && s->tpr == 1 && !s->dyn && l2_hint_pays(s->vt_f32, npad)) ? 1 : 0;
+    s->l2hint = (s->layout == LAY_CSR && s->tpr == 1 && !s->dyn && !bj && l2_hint_pays(s->vt_f32, npad)) ? 1 : 0;
     alloc(&s->vecmem, (size_t)NVEC * npad * s->vbytes);
     if (s->layout == LAY_SELL) {
         alloc((void**)&s->x64w, sizeof(double) * nn);
@@ -249,6 +271,7 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (!rc && cudaMemset(s->partials, 0, sizeof(double) * 2 * (size_t)grid * NSLOT * kRec) != cudaSuccess) rc = BCS_ERR_CUDA;
     s->precond = o.precond;
     if (!rc && s->precond == BCS_PRECOND_JACOBI) rc = precond_setup(s);
+    if (!rc && bj) rc = bjacobi_setup(s);
     if (rc) {
         bcs_solver_destroy(s);
         return rc;
@@ -306,6 +329,13 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
     P->scal = s->scal;
     P->out = s->out;
     P->l2hint = s->l2hint;
+    if (s->bj_bs) {
+        P->bs = s->bj_bs;
+        P->bj64 = s->bjE;
+        P->bj = s->vt_f32 ? (const void*)s->bjE32 : (const void*)s->bjE;
+        for (int k = 0; k < 5; ++k) P->hat[k] = (char*)s->bjhat + (size_t)k * npad * s->vbytes;
+        P->xhat64 = s->bjxh;
+    }
 }
 
 static int finish(bcs_solver s, cudaStream_t st, bcs_result* res) {
@@ -349,8 +379,10 @@ static int launch(bcs_solver s, const double* b, double* x, cudaStream_t st) {
     cudaEventRecord(s->ev0, st);
     // right preconditioning: the kernel iterates on y = D x
     if (s->precond == BCS_PRECOND_JACOBI && precond_scale(s, x, 1, st) != 0) return BCS_ERR_CUDA;
-    const int e = dispatch(&P, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, s->grid, st, nullptr);
+    if (s->bj_bs && bjacobi_apply(s, x, 0, st) != 0) return BCS_ERR_CUDA;   // y0 = M x0
+    const int e = dispatch(&P, s->vt_f32, s->valtype, s->layout, s->tpr, s->dyn, s->grid, st, nullptr, s->bj_bs != 0);
     if (e == 0 && s->precond == BCS_PRECOND_JACOBI && precond_scale(s, x, 0, st) != 0) return BCS_ERR_CUDA;
+    if (e == 0 && s->bj_bs && bjacobi_apply(s, x, 1, st) != 0) return BCS_ERR_CUDA;   // x = M^-1 y
     cudaEventRecord(s->ev1, st);
     return e == 0 ? BCS_OK : BCS_ERR_CUDA;
 }
@@ -406,6 +438,17 @@ int bcs_get_scalars(bcs_solver s, double* out, int cap, int* len) {
     const int m = std::min(avail, cap);
     if (out && m > 0 && cudaMemcpy(out, s->scal, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost) != cudaSuccess)
         return BCS_ERR_CUDA;
+    return BCS_OK;
+}
+
+int bcs_solver_precond_blocks(bcs_solver s, double* D, double* E, int* bs) {
+    if (!s || !s->bj_bs) return BCS_ERR_ARG;
+    if (bs) *bs = s->bj_bs;
+    const size_t bytes = sizeof(double) * (size_t)s->A->n * (size_t)s->bj_bs;
+    if (bytes == 0) return BCS_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return BCS_ERR_CUDA;
+    if (D && cudaMemcpy(D, s->bjD, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return BCS_ERR_CUDA;
+    if (E && cudaMemcpy(E, s->bjE, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return BCS_ERR_CUDA;
     return BCS_OK;
 }
 

@@ -72,6 +72,15 @@ struct KParams {
     double* scal;           // [4*hist_cap]
     double* out;            // [NOUT]
     int l2hint;             // launch the L2-hinted kernel (FP32 vectors, CSR, one lane per row; see l2_hint_pays)
+    // block-Jacobi right preconditioning (bs = 0: none): M^-1 in the inner
+    // value type and in FP64, [rows][bs] in block columns (rows padded to
+    // whole tiles, zero there); the M^-1 copies of r, s, s2, w and u (inner
+    // type) and of the FP64 iterate
+    int bs;
+    const void* bj;
+    const double* bj64;
+    void* hat[5];
+    double* xhat64;
     // row-partitioned solve (include/bcs_dist.h): this rank's first global
     // row, which of its rows other ranks need (per local row: entries
     // send_ptr[row] .. send_ptr[row+1] of send_dst = (rank, offset in that
@@ -177,6 +186,12 @@ struct bcs_solver_s {
     double* pdiag = nullptr;      // Jacobi: diag(A) in the caller's row order
     double* pval64 = nullptr;     // Jacobi: A D^-1 in the solver's layout, FP64
     void* pvalin = nullptr;       // Jacobi: A D^-1 in the inner value type (refinement modes)
+    int bj_bs = 0;                // block-Jacobi: rows per block (0: not block-Jacobi)
+    double* bjD = nullptr;        // block-Jacobi: the diagonal blocks, [npad][bs] FP64
+    double* bjE = nullptr;        // block-Jacobi: their inverses, [npad][bs] FP64
+    float* bjE32 = nullptr;       // block-Jacobi: the inverses in FP32 (refinement modes)
+    void* bjhat = nullptr;        // block-Jacobi: five M^-1 copies in the inner vector type
+    double* bjxh = nullptr;       // block-Jacobi: M^-1 y (FP64)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int hist_len = 0;
     int last_iters = 0;

@@ -219,7 +219,15 @@ struct ClusterGroup {
 // matrix-vector product gathers pushed into that rank's halo as it is written.
 // H: the L2 evict_first policy on the matrix and the single-use vector
 // streams (FP32/BF16 vectors; instantiated for CSR with one lane per row).
-template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false, bool H = false>
+// BJ: block-Jacobi right preconditioning (bcs.h, BCS_PRECOND_BLOCK_JACOBI):
+// the method runs on A M^-1; every vector that a product gathers is also
+// written as M^-1 v by the pass that writes it (blocks of P.bs rows lie inside
+// the 32-row tiles, so the warp that holds a tile's values forms them), and
+// the products gather those copies.  The solved system's iterate y is x64;
+// the caller turns x = M^-1 y after the launch (CSR, one lane per row, static
+// tile order; kinds ssBiCGSafe2 and p-BiCGSafe).
+template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false, bool H = false,
+          bool BJ = false>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
@@ -279,6 +287,26 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     };
     auto spmv64 = [&](const double* xv, int64_t tile) -> double {
         return tile_spmv<double, double, LAYOUT, T>(P, P.val64, xv, tile, sbuf64);
+    };
+    // block-Jacobi: the M^-1 copies of r, s (two, alternating like s), w and u
+    VT* const RH = BJ ? (VT*)P.hat[0] : nullptr;
+    VT* SHc = BJ ? (VT*)P.hat[1] : nullptr;
+    VT* SHn = BJ ? (VT*)P.hat[2] : nullptr;
+    VT* const WH = BJ ? (VT*)P.hat[3] : nullptr;
+    VT* const UH = BJ ? (VT*)P.hat[4] : nullptr;
+    const VT* const BJE = (const VT*)P.bj;
+    // (M^-1 v) on this lane's row, M^-1 stored [rows][bs] in block columns: the
+    // block's values come from the lanes of the same block by shuffles and are
+    // summed with fma in column order from zero.  Every lane of the warp calls
+    // it; rows >= n pass v = 0 (their stored entries are zero as well).
+    auto bj_apply = [&](const auto* E, auto v, RowT row) {
+        using ET = decltype(v);
+        const int bs = P.bs;
+        const int base = lane & ~(bs - 1);
+        const ET* e = E + (size_t)row * bs;
+        ET acc = ET(0);
+        for (int j = 0; j < bs; ++j) acc = vfma(e[j], __shfl_sync(0xffffffffu, v, base + j), acc);
+        return acc;
     };
     // partitioned solve: a value that another rank's next matrix-vector
     // product gathers is stored straight into that rank's halo (vector id v,
@@ -435,6 +463,15 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     int since_best = 0;
 
     for (;;) {
+        if constexpr (BJ) {
+            // the products of the true residual gather M^-1 y
+            for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
+                const RowT row = (RowT)(tile * 32) + lane;
+                const double h = bj_apply(P.bj64, row < n ? P.x64[row] : 0.0, row);
+                if (row < n) P.xhat64[row] = h;
+            }
+            if (!grp.sync(&s_flag)) { stg.settle(); return; }
+        }
         // ---------------- true residual r = b - A x (FP64) and (re)initialisation ----------
         {
             typename DotAccOf<VT>::type xv[10];
@@ -442,7 +479,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             WAcc xt[10];  // the FP64 true-residual norm is always accumulated exactly
             wa_init10(xt);
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                const double ax = spmv64(P.x64, tile);
+                const double ax = spmv64(BJ ? (const double*)P.xhat64 : P.x64, tile);
                 const RowT row = (RowT)(tile * 32) + lane;
                 double qa_ST = double(0), qb_ST = double(0);
                 VT qa_SF = VT(0), qb_SF = VT(0);
@@ -462,6 +499,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     Z[row] = VT(0); W[row] = VT(0); L[row] = VT(0); G[row] = VT(0);
                     qa_SF = rv;
                     qb_SF = rv;
+                }
+                if constexpr (BJ) {   // qa_SF = r on the lane's row (0 beyond n)
+                    const VT h = bj_apply(BJE, qa_SF, row);
+                    if (row < n) RH[row] = h;
                 }
                 wa_acc(xt[ST], qa_ST, qb_ST, row < n);
                 wa_acc(xv[SF], qa_SF, qb_SF, row < n);
@@ -496,8 +537,12 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
             wa_init10(xv);
             ++n_spmv;
             for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                const VT sv = spmv(R, tile);
+                const VT sv = spmv(BJ ? RH : R, tile);
                 const RowT row = (RowT)(tile * 32) + lane;
+                if constexpr (BJ) {
+                    const VT h = bj_apply(BJE, sv, row);
+                    if (row < n) SHc[row] = h;
+                }
                 VT qa_SA = VT(0), qb_SA = VT(0);
                 VT qa_SD = VT(0), qb_SD = VT(0);
                 VT qa_SG = VT(0), qb_SG = VT(0);
@@ -546,7 +591,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t t2 = tiles_next(t1, tc);
                     int rpa_n = 0, rpb_n = 0;
                     if (kRp) rp_load(t1, rpa_n, rpb_n);
-                    const VT sv = spmv_rp(R, tile, rpa, rpb);
+                    const VT sv = spmv_rp(BJ ? RH : R, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1));
                     const RowT row = (RowT)(tile * 32) + lane;
@@ -592,7 +637,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     stage_two(FirstA{}, vA0, pa0, pa1);
                     const bool reducer = kRedOff > 0 && warp >= kRedOff && warp < kRedOff + 9;
                     have_first = !reducer && pa0 < ntiles;
-                    if (have_first) as_first = spmv(sCur, pa0);
+                    if (have_first) as_first = spmv(BJ ? SHc : sCur, pa0);
                     reduce_finish<9, NW, kRedOff>(rbase(cur), nblk, s_x, s_sum);
                 } else {
                     reduce_partials<9>(rbase(cur), nblk, s_x, s_sum);
@@ -705,6 +750,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t b2 = tiles_next(b1, tb);
                     const VT* sm = stg.wait((int)(kt & 1));
                     const RowT row = (RowT)(tile * 32) + lane;
+                    VT u_out = VT(0);
                     if (row < n) {
                         const VT r = sm[lane], s = sm[32 + lane], t = sm[64 + lane], y = sm[96 + lane];
                         VT p = sm[128 + lane], u = sm[160 + lane];
@@ -713,7 +759,13 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         u = vfma(ze, o, et * vfma(be, u, y));
                         Pv[row] = p; O[row] = o; U[row] = u;
                         push(V_U, tile, row, u);
+                        u_out = u;
                     }
+                    if constexpr (BJ) {
+                        const VT h = bj_apply(BJE, u_out, row);
+                        if (row < n) UH[row] = h;
+                    }
+                    (void)u_out;
                     stage_at(FirstPB{}, vPB, b2, kt);
                     b0 = b1;
                     b1 = b2;
@@ -734,7 +786,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t c2 = tiles_next(c1, tcc);
                     int rpa_n = 0, rpb_n = 0;
                     if (kRp) rp_load(c1, rpa_n, rpb_n);
-                    const VT w = spmv_rp(U, tile, rpa, rpb);
+                    const VT w = spmv_rp(BJ ? UH : U, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1));
                     const RowT row = (RowT)(tile * 32) + lane;
@@ -771,6 +823,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    if constexpr (BJ) {   // qa_SR = r_{i+1} on the lane's row (0 beyond n)
+                        const VT h = bj_apply(BJE, qa_SR, row);
+                        if (row < n) RH[row] = h;
+                    }
                     stage_at(FirstPC{}, vPC, c2, kt);
                     c0 = c1;
                     c1 = c2;
@@ -789,7 +845,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t pa2 = tiles_next(pa1, pac);
                     int rpa_n = 0, rpb_n = 0;
                     if (kRp && kt > 0) rp_load(pa1, rpa_n, rpb_n);
-                    const VT As = (kt == 0) ? (have_first ? as_first : spmv(sCur, tile)) : spmv_rp(sCur, tile, rpa, rpb);
+                    const VT* const sx = BJ ? SHc : sCur;
+                    const VT As = (kt == 0) ? (have_first ? as_first : spmv(sx, tile)) : spmv_rp(sx, tile, rpa, rpb);
                     if (kt > 0) { rpa = rpa_n; rpb = rpb_n; }
                     const VT* sm = stg.wait((int)(kt & 1));
                     const RowT row = (RowT)(tile * 32) + lane;
@@ -798,6 +855,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     VT qa_SF = VT(0), qb_SF = VT(0);
                     VT qa_SH = VT(0), qb_SH = VT(0);
                     VT qa_SR = VT(0), qb_SR = VT(0);
+                    VT w_out = VT(0);
                     if (row < n) {
                         const VT r = sm[lane], s = sm[32 + lane], rs = sm[64 + lane];
                         VT p = sm[96 + lane], u = sm[128 + lane], t = sm[160 + lane], l = sm[192 + lane];
@@ -814,6 +872,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         x = vfma(al, p, x) + z;
                         const VT rn = vfma(-al, o, r) - yn;
                         st1(Pv + row, p); st1(U + row, u); W[row] = w; st1(Tv + row, t); st1(Z + row, z);
+                        w_out = w;
                         Y[row] = yn; st1(X + row, x); R[row] = rn; O[row] = As;
                         push(V_W, tile, row, w);
                         push(xId, tile, row, x);
@@ -833,6 +892,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    if constexpr (BJ) {
+                        const VT h = bj_apply(BJE, w_out, row);
+                        if (row < n) WH[row] = h;
+                    }
+                    (void)w_out;
                     stage_at(FirstA{}, vA, pa2, kt);
                     pa0 = pa1;
                     pa1 = pa2;
@@ -857,7 +921,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const int64_t c2 = tiles_next(c1, tcc);
                     int rpa_n = 0, rpb_n = 0;
                     if (kRp) rp_load(c1, rpa_n, rpb_n);
-                    const VT Aw = spmv_rp(W, tile, rpa, rpb);
+                    const VT Aw = spmv_rp(BJ ? WH : W, tile, rpa, rpb);
                     rpa = rpa_n; rpb = rpb_n;
                     const VT* sm = stg.wait((int)(kt & 1));
                     const RowT row = (RowT)(tile * 32) + lane;
@@ -889,6 +953,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SC], qa_SC, qb_SC, row < n);
                     wa_acc(xv[SD], qa_SD, qb_SD, row < n);
                     wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                    if constexpr (BJ) {   // qa_SA = s_{i+1} on the lane's row (0 beyond n)
+                        const VT h = bj_apply(BJE, qa_SA, row);
+                        if (row < n) SHn[row] = h;
+                    }
                     stage_at(FirstC{}, vC, c2, kt);
                     c0 = c1;
                     c1 = c2;
@@ -897,6 +965,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
                 const int tid = sCurId; sCurId = sNxtId; sNxtId = tid;
+                if constexpr (BJ) { VT* th = SHc; SHc = SHn; SHn = th; }
             } else {
                 // residual replacement iteration (Alg. 5)
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
@@ -1046,10 +1115,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     }
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false, bool BJ = false>
 __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
-    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN, GridGroup, false, H>(P, grp);
+    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN, GridGroup, false, H, BJ>(P, grp);
 }
 
 // Partitioned solve (bcs_dist.h): one cooperative launch whose CTAs are split
@@ -1083,28 +1152,29 @@ constexpr size_t stage_smem_bytes() {
     return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT);
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false, bool BJ = false>
 int launch_one(const KParams& P, int grid, cudaStream_t st) {
     void* args[] = {(void*)&P};
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
-    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H>,
+    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H, BJ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H>, dim3(grid),
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H, BJ>, dim3(grid),
                                             dim3(kSolveBlock), args, smem, st);
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool BJ = false>
 int max_grid_one(int* grid) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN>,
+        e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, false, BJ>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T, DYN>, kSolveBlock, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_kernel<VT, MT, LAYOUT, T, DYN, false, BJ>,
+                                                          kSolveBlock, smem);
     *grid = sms * per;
     return (int)e;
 }
@@ -1135,7 +1205,8 @@ int dispatch_dist(const DistArgs* D, int grid, cudaStream_t st, int* max_grid) {
 // translation unit instantiates one subset (SUBSET 0: SELL and CSR with 1 lane
 // per row, SUBSET 1: CSR with 4, 8 or 32 lanes per row or adaptive (-1), both
 // in the static tile order; SUBSET 2: the dynamic tile order for SELL and CSR
-// with 1, 8 or adaptive lanes per row).
+// with 1, 8 or adaptive lanes per row; SUBSET 3: block-Jacobi, CSR with 1
+// lane per row in the static order).
 template <class VT, class MT, int SUBSET>
 int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
 #define BCS_CASE(LAY, TT, D)                                                              \
@@ -1153,6 +1224,11 @@ int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, i
             case 8: BCS_CASE(LAY_CSR, 8, false);
             default: BCS_CASE(LAY_CSR, 32, false);
         }
+    } else if constexpr (SUBSET == 3) {
+        (void)layout;
+        (void)tpr;
+        return P ? launch_one<VT, MT, LAY_CSR, 1, false, false, true>(*P, grid, st)
+                 : max_grid_one<VT, MT, LAY_CSR, 1, false, true>(max_grid);
     } else {
         if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1, true); }
         if (tpr == 8) { BCS_CASE(LAY_CSR, 8, true); }

@@ -1,0 +1,9 @@
+// Persistent solver kernels, double vectors and double matrix values, block-Jacobi
+// right preconditioning (instantiation subset 3).
+#include "solver.cuh"
+
+namespace bcs {
+int dispatch_f64_3(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, int* max_grid) {
+    return dispatch<double, double, 3>(P, layout, tpr, grid, st, max_grid);
+}
+}  // namespace bcs

@@ -1,0 +1,165 @@
+"""GPU parity of block-Jacobi right preconditioning (bcs.h, BCS_PRECOND_BLOCK_JACOBI)
+against the oracle's orc_solve_bjacobi on the same seeded inputs:
+  - the diagonal blocks and their Gauss-Jordan inverses: bit-exact (the same
+    operations per element on both sides);
+  - FP64 solves: every product gathers M^-1 v formed with the oracle's fma
+    order, the inner products are correctly rounded on both sides, so the
+    residual histories, scalars, iteration counts and x are bit-identical;
+  - refinement modes: FP64 true residual of the original system <= 1e-10 and x
+    within 1e-7 of the FP64 oracle's.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2108_10591_gb300 as bcs
+    return bcs, torch, orc
+
+
+def _pivoting_matrix(n, seed):
+    """Random nonsymmetric matrix whose diagonal blocks need row swaps (small diagonal)."""
+    rng = np.random.default_rng(seed)
+    Ad = np.where(rng.random((n, n)) < 0.2, rng.standard_normal((n, n)), 0.0)
+    Ad += np.diag(rng.uniform(0.05, 0.5, n))
+    for i in range(n):   # strong couplings inside the 8-row blocks keep the matrix well conditioned
+        j = (i // 8) * 8 + (i + 3) % 8
+        if j < n:
+            Ad[i, j] += 4.0
+    return W.dense_to_csr(Ad)
+
+
+MATS = {
+    "cd2d_64": lambda: W.cd2d(64, 20.0),
+    "powerlaw_20001": lambda: W.powerlaw(n=20001, seed=9),
+    "pivoting_203": lambda: _pivoting_matrix(203, 4),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("bs", [1, 2, 4, 8, 16, 32])
+def test_bjacobi_blocks_bit_exact(env, name, bs):
+    """D and E = D^-1 (Gauss-Jordan, partial pivoting) equal the oracle's bit for bit, ragged
+    last blocks included."""
+    bcs, torch, orc = env
+    A = MATS[name]()
+    try:
+        D0, E0 = orc.bjacobi_blocks(A, bs)
+    except ValueError:
+        pytest.skip("singular block for this size")
+    M = bcs.csr_upload(A)
+    S = bcs.solver_create(M, "p-BiCGSafe", precond="block-jacobi", block_size=bs)
+    D, E = bcs.precond_blocks(S)
+    assert np.array_equal(D, D0)
+    assert np.array_equal(E, E0)
+
+
+def _gpu_solve(bcs, torch, A, b, kind, x0=None, **kw):
+    M = bcs.csr_upload(A, stores=bcs.STORE_F32 | bcs.STORE_BF16)
+    S = bcs.solver_create(M, kind, tol=kw.pop("tol", 1e-10), maxit=kw.pop("maxit", 5000), precond="block-jacobi",
+                          **kw)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd) if x0 is None else torch.from_numpy(x0.copy()).cuda()
+    res = bcs.solve(S, bd, xd)
+    return res, xd.cpu().numpy(), bcs.get_history(S), bcs.get_scalars(S)
+
+
+@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe"])
+@pytest.mark.parametrize("name,bs,cfg", [("cd2d_64", 8, {}), ("cd2d_64", 1, {}), ("cd2d_64", 32, dict(max_ctas=3)),
+                                         ("powerlaw_20001", 4, dict(max_ctas=16)),
+                                         ("pivoting_203", 8, dict(max_ctas=1))])
+def test_bjacobi_solve_bit_identical(env, kind, name, bs, cfg):
+    """FP64: histories, scalars, iteration and outer-step counts and x bit-identical to the
+    oracle's preconditioned runs (several grid sizes, ragged n)."""
+    bcs, torch, orc = env
+    A = MATS[name]()
+    b = W.rhs_ones(A)
+    res, x, h, sc = _gpu_solve(bcs, torch, A, b, kind, block_size=bs, **cfg)
+    ref = orc.solve_bjacobi(A, b, bs, kind=kind, tol=1e-10, maxit=5000, max_restarts=29)
+    assert res["status"] == 0 and ref["status"] == 0, (res, ref["status_name"])
+    assert res["iterations"] == ref["iterations"]
+    assert res["outer_steps"] == ref["restarts"] + 1
+    assert np.array_equal(h, ref["hist"])
+    assert np.array_equal(sc[:len(ref["scalars"])], ref["scalars"][:len(sc)])
+    assert np.array_equal(x, ref["x"])
+    assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
+
+
+def test_bjacobi_start_vector(env):
+    """A non-zero x_0 enters as y_0 = M x_0 on both sides: bit-identical runs."""
+    bcs, torch, orc = env
+    A = W.cd2d(48, 30.0)
+    b = W.rhs_ones(A)
+    x0 = np.random.default_rng(2).standard_normal(A.n)
+    res, x, h, _ = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", x0=x0, block_size=4)
+    ref = orc.solve_bjacobi(A, b, 4, x0=x0, kind="p-BiCGSafe", tol=1e-10, maxit=5000, max_restarts=29)
+    assert res["iterations"] == ref["iterations"]
+    assert np.array_equal(h, ref["hist"]) and np.array_equal(x, ref["x"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe"])
+def test_bjacobi_refinement_modes(env, prec, kind):
+    """FP32/BF16 inner solves on A M^-1 (M^-1 rounded to FP32) inside FP64 refinement: the FP64
+    true residual of the original system reaches 1e-10 and x is within 1e-7 of the FP64
+    oracle's."""
+    bcs, torch, orc = env
+    A = W.cd2d(64, 20.0)
+    b = W.rhs_ones(A)
+    res, x, _, _ = _gpu_solve(bcs, torch, A, b, kind, precision=prec, block_size=8)
+    ref = orc.solve_bjacobi(A, b, 8, kind=kind, tol=1e-10, maxit=5000, max_restarts=29)
+    assert res["status"] == 0, res
+    assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
+    assert np.max(np.abs(x - ref["x"])) <= 1e-7
+    assert res["outer_steps"] >= 2
+
+
+def test_bjacobi_refusals(env):
+    """Combinations the preconditioned kernel is not built for, block sizes that do not divide
+    a tile and singular blocks are refused at bcs_solver_create; the library's defaults are
+    adjusted instead of refused."""
+    bcs, torch, orc = env
+    A = W.cd2d(20, 20.0)
+    M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL)
+    bad = [dict(kind="p-BiCGSafe-rr"), dict(layout="sell"), dict(threads_per_row=8), dict(tile_order=2),
+           dict(block_size=3), dict(block_size=64)]
+    for kw in bad:
+        kind = kw.pop("kind", "p-BiCGSafe")
+        with pytest.raises(bcs.BcsError):
+            bcs.solver_create(M, kind, precond="block-jacobi", **kw)
+    S = bcs.solver_create(M, "p-BiCGSafe", precond="block-jacobi", threads_per_row=1, tile_order=1)
+    assert bcs.precond_blocks(S)[0].shape == (A.n, 8)   # default block size 8
+    Ad = np.eye(16)
+    Ad[2:4, 2:4] = [[1.0, 2.0], [2.0, 4.0]]
+    Ad[3, 9] = 1.0
+    with pytest.raises(bcs.BcsError):
+        bcs.solver_create(bcs.csr_upload(W.dense_to_csr(Ad)), "p-BiCGSafe", precond="block-jacobi", block_size=2)
+    S0 = bcs.solver_create(M, "p-BiCGSafe")
+    with pytest.raises(bcs.BcsError):
+        bcs.precond_blocks(S0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bjacobi_cd3d_128(env, prec):
+    """The 128^3 upwind system (n = 2,097,152) with blocks of 8 rows along x: the FP64 true
+    residual of the original system reaches 1e-10."""
+    bcs, torch, orc = env
+    A = W.cd3d_upwind(128, 50.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A, stores=bcs.STORE_F32)
+    S = bcs.solver_create(M, "p-BiCGSafe", tol=1e-10, maxit=10000, precision=prec, precond="block-jacobi",
+                          block_size=8)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, xd)
+    x = xd.cpu().numpy()
+    assert res["status"] == 0, res
+    assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
