@@ -77,6 +77,7 @@ SIDE_WORKLOADS = {
                    "within n/100 of the diagonal, N(0,1) values, diagonal 1.2 x row abs-sum",
     "cd3d27_192": "3D 27-point convection-diffusion, 192^3 (n=7,077,888), beta=100 on the face couplings",
     "batch_cd2d_512": "512 independent 2D 5-point convection-diffusion systems, side U{32..256}, beta U[0,50]",
+    "cd3d_128_pc": "the benchmark's 128^3 upwind system as a side workload (preconditioned runs)",
 }
 
 
@@ -121,7 +122,9 @@ def args_parse():
     ap.add_argument("--workload", default="cd3d_128", choices=list(SIDE_WORKLOADS) + ["cd3d_128"],
                     help="cd3d_128 (the benchmark line); the others print a side measurement line")
     ap.add_argument("--tune", action="store_true", help="side workloads: autotune the layout / lanes per row first")
-    ap.add_argument("--precond", default="none", choices=["none", "jacobi"], help="side workloads: preconditioner")
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi", "block-jacobi"],
+                    help="side workloads: preconditioner")
+    ap.add_argument("--block-size", type=int, default=8, help="block-jacobi: rows per diagonal block")
     ap.add_argument("--big-ctas", type=int, default=-1,
                     help="batch: CTAs per cluster of the second lane for the largest systems (0 = one lane; "
                          "default: 8 with FP32/BF16 inner solves, where it was measured 10 %% faster, 0 in FP64, "
@@ -345,7 +348,8 @@ def reference_arm(a):
 
 def side_single(a, bcs, torch, dist, world, rank):
     import workloads as W
-    A = W.powerlaw() if a.workload == "powerlaw_4m" else W.cd3d27(192, 100.0)
+    A = (W.powerlaw() if a.workload == "powerlaw_4m" else W.cd3d_upwind(128, 50.0) if a.workload == "cd3d_128_pc"
+         else W.cd3d27(192, 100.0))
     b = W.rhs_ones(A)
     layouts = bcs.LAYOUT_CSR | bcs.LAYOUT_SELL
     M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32 | bcs.STORE_BF16)
@@ -356,8 +360,9 @@ def side_single(a, bcs, torch, dist, world, rank):
         layout, tpr = "auto", 0
     else:
         layout, tpr = a.layout, a.tpr
+    pc = dict(precond=a.precond, block_size=a.block_size) if a.precond == "block-jacobi" else dict(precond=a.precond)
     S = bcs.solver_create(M, a.kind, tol=1e-10, maxit=a.maxit, precision=a.precision, layout=layout,
-                          threads_per_row=tpr, max_outer=30, precond=a.precond)
+                          threads_per_row=tpr, max_outer=30, **pc)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
     for _ in range(a.warmup):
@@ -379,6 +384,9 @@ def side_single(a, bcs, torch, dist, world, rank):
     lo = a.precision != "fp64"
     vb, mb = (4, 4 if a.precision == "fp32" else 2) if lo else (8, 8)
     _, by = solve_work(a.kind, A.n, A.nnz, res["iterations"], res["outer_steps"], vb, mb)
+    if a.precond == "block-jacobi":
+        # two M^-1 applications per iteration: each reads bs entries of M^-1 per row and writes one copy
+        by += 2.0 * res["iterations"] * A.n * (a.block_size + 1) * vb
     peaks, src = measured_peaks()
     gbs = by / t / 1e9
     hp = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
@@ -388,7 +396,8 @@ def side_single(a, bcs, torch, dist, world, rank):
             "rel_res_true": res["rel_res_true"],
             "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "n": A.n, "nnz": A.nnz,
                        "kind": a.kind, "precision": a.precision, "layout": layout, "threads_per_row": tpr,
-                       "precond": a.precond},
+                       "precond": a.precond,
+                       "block_size": a.block_size if a.precond == "block-jacobi" else None},
             "hbm": {"achieved": gbs, "peak": hp, "unit": "GB/s", "frac": gbs / hp, "peak_source": src},
             "tune": tune}
 

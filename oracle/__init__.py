@@ -276,7 +276,7 @@ def bjacobi_apply(M, v, bs):
 
 
 def solve_bjacobi(A, b, bs, x0=None, kind="p-BiCGSafe", tol=1e-10, maxit=10000, rr_m=100, rr_M=None,
-                  max_restarts=0, hist_cap=None):
+                  max_restarts=0, hist_cap=None, parallel=False):
     """Algorithm 3/4/5 with block-Jacobi right preconditioning (see orc_solve_bjacobi): the runs
     on A M^-1 from y_0 = M x_0, x = M^-1 y.  Returns the same dict as solve() without the state
     dump."""
@@ -291,7 +291,7 @@ def solve_bjacobi(A, b, bs, x0=None, kind="p-BiCGSafe", tol=1e-10, maxit=10000, 
     scal = np.zeros(4 * cap)
     hl = ctypes.c_int(0)
     res = _Result()
-    st = lib().orc_solve_bjacobi(n, _p(rp), _p(ci), _p(va), int(bs), _p(b), _p(x), ctypes.byref(o), _p(hist), cap,
+    st = lib(parallel).orc_solve_bjacobi(n, _p(rp), _p(ci), _p(va), int(bs), _p(b), _p(x), ctypes.byref(o), _p(hist), cap,
                                  ctypes.byref(hl), _p(scal), ctypes.byref(res))
     k = min(res.iterations + 1, cap)
     return dict(x=x, hist=hist[:hl.value].copy(), status=st, status_name=STATUS.get(st, str(st)),

@@ -147,6 +147,26 @@ def test_bjacobi_refusals(env):
         bcs.precond_blocks(S0)
 
 
+@pytest.mark.parametrize("bs", [2, 8])
+def test_bjacobi_cd3d_128_first_iterations(env, bs):
+    """n = 2,097,152 in the default launch configuration: the first 30 preconditioned
+    p-BiCGSafe iterations' histories and scalars bit-identical to the oracle's."""
+    bcs, torch, orc = env
+    A = W.cd3d_upwind(128, 50.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A)
+    S = bcs.solver_create(M, "p-BiCGSafe", tol=0.0, maxit=30, max_outer=1, precond="block-jacobi", block_size=bs)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    h, sc = bcs.get_history(S), bcs.get_scalars(S)
+    ref = orc.solve_bjacobi(A, b, bs, kind="p-BiCGSafe", tol=0.0, maxit=30, parallel=True)
+    assert res["iterations"] == ref["iterations"] == 30
+    assert len(h) == len(ref["hist"]) >= 30
+    assert np.array_equal(h, ref["hist"])
+    assert np.array_equal(sc[:30], ref["scalars"][:30])
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_bjacobi_cd3d_128(env, prec):
     """The 128^3 upwind system (n = 2,097,152) with blocks of 8 rows along x: the FP64 true
