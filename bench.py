@@ -38,9 +38,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "cd3d128_full_solves.json")
 # workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
 # iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
 # for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
-TRAFFIC = {"fp64": {"per_iter": 914.5e6, "per_outer": 1020.3e6},
-           "fp32": {"per_iter": 381.7e6, "per_outer": 871.2e6}}
-KERNEL_SHA = "9cb4f5f2fb48380f"
+TRAFFIC = {"fp64": {"per_iter": 914.5e6, "per_outer": 1020.4e6},
+           "fp32": {"per_iter": 381.9e6, "per_outer": 867.9e6}}
+KERNEL_SHA = "2dc9dce5ae529e6e"
 
 
 # The measured kernel's sources and its launch path.  Other translation units
