@@ -202,10 +202,8 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (!(A->layouts & o.layout)) return BCS_ERR_ARG;
     const bool bj = o.precond == BCS_PRECOND_BLOCK_JACOBI;
     if (bj) {
-        // built for CSR with one lane per row in the static tile order, and for
-        // the kinds whose products are all in the fused phases
-        if (o.layout != BCS_LAYOUT_CSR || (o.threads_per_row != 0 && o.threads_per_row != 1) || o.tile_order == 2 ||
-            kind == BCS_P_BICGSAFE_RR)
+        // built for CSR with one lane per row in the static tile order
+        if (o.layout != BCS_LAYOUT_CSR || (o.threads_per_row != 0 && o.threads_per_row != 1) || o.tile_order == 2)
             return BCS_ERR_ARG;
         if (o.block_size == 0) o.block_size = 8;
     }
@@ -333,7 +331,7 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
         P->bs = s->bj_bs;
         P->bj64 = s->bjE;
         P->bj = s->vt_f32 ? (const void*)s->bjE32 : (const void*)s->bjE;
-        for (int k = 0; k < 5; ++k) P->hat[k] = (char*)s->bjhat + (size_t)k * npad * s->vbytes;
+        for (int k = 0; k < 8; ++k) P->hat[k] = (char*)s->bjhat + (size_t)k * npad * s->vbytes;
         P->xhat64 = s->bjxh;
     }
 }

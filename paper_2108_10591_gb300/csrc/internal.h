@@ -74,12 +74,12 @@ struct KParams {
     int l2hint;             // launch the L2-hinted kernel (FP32 vectors, CSR, one lane per row; see l2_hint_pays)
     // block-Jacobi right preconditioning (bs = 0: none): M^-1 in the inner
     // value type and in FP64, [rows][bs] in block columns (rows padded to
-    // whole tiles, zero there); the M^-1 copies of r, s, s2, w and u (inner
-    // type) and of the FP64 iterate
+    // whole tiles, zero there); the M^-1 copies of r, s, s2, w, u, t, y and the
+    // inner iterate (inner type) and of the FP64 iterate
     int bs;
     const void* bj;
     const double* bj64;
-    void* hat[5];
+    void* hat[8];
     double* xhat64;
     // row-partitioned solve (include/bcs_dist.h): this rank's first global
     // row, which of its rows other ranks need (per local row: entries
@@ -190,7 +190,7 @@ struct bcs_solver_s {
     double* bjD = nullptr;        // block-Jacobi: the diagonal blocks, [npad][bs] FP64
     double* bjE = nullptr;        // block-Jacobi: their inverses, [npad][bs] FP64
     float* bjE32 = nullptr;       // block-Jacobi: the inverses in FP32 (refinement modes)
-    void* bjhat = nullptr;        // block-Jacobi: five M^-1 copies in the inner vector type
+    void* bjhat = nullptr;        // block-Jacobi: eight M^-1 copies in the inner vector type
     double* bjxh = nullptr;       // block-Jacobi: M^-1 y (FP64)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int hist_len = 0;

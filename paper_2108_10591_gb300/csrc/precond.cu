@@ -214,7 +214,7 @@ int precond_scale(bcs_solver s, double* x, int into, cudaStream_t st) {
 }
 
 // Block-Jacobi set-up: D and E = D^-1 ([npad][bs], FP64; rows >= n zero), E in
-// FP32 for the refinement modes, and the solver's M^-1 copies (five inner-type
+// FP32 for the refinement modes, and the solver's M^-1 copies (eight inner-type
 // vectors and one FP64 vector).  BCS_ERR_ARG for a singular block.
 int bjacobi_setup(bcs_solver s) {
     bcs_matrix A = s->A;
@@ -231,12 +231,12 @@ int bjacobi_setup(bcs_solver s) {
     alloc((void**)&s->bjD, sizeof(double) * m);
     alloc((void**)&s->bjE, sizeof(double) * m);
     if (s->vt_f32) alloc((void**)&s->bjE32, sizeof(float) * m);
-    alloc(&s->bjhat, 5 * (size_t)npad * s->vbytes);
+    alloc(&s->bjhat, 8 * (size_t)npad * s->vbytes);
     alloc((void**)&s->bjxh, sizeof(double) * (size_t)npad);
     alloc((void**)&flags, sizeof(int));
     if (!rc && (cudaMemset(s->bjD, 0, sizeof(double) * m) != cudaSuccess ||
                 cudaMemset(s->bjE, 0, sizeof(double) * m) != cudaSuccess ||
-                cudaMemset(s->bjhat, 0, 5 * (size_t)npad * s->vbytes) != cudaSuccess ||
+                cudaMemset(s->bjhat, 0, 8 * (size_t)npad * s->vbytes) != cudaSuccess ||
                 cudaMemset(s->bjxh, 0, sizeof(double) * (size_t)npad) != cudaSuccess ||
                 cudaMemset(flags, 0, sizeof(int)) != cudaSuccess))
         rc = BCS_ERR_CUDA;

@@ -225,7 +225,7 @@ struct ClusterGroup {
 // the 32-row tiles, so the warp that holds a tile's values forms them), and
 // the products gather those copies.  The solved system's iterate y is x64;
 // the caller turns x = M^-1 y after the launch (CSR, one lane per row, static
-// tile order; kinds ssBiCGSafe2 and p-BiCGSafe).
+// tile order; all three kinds).
 template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false, bool H = false,
           bool BJ = false>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
@@ -288,12 +288,16 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     auto spmv64 = [&](const double* xv, int64_t tile) -> double {
         return tile_spmv<double, double, LAYOUT, T>(P, P.val64, xv, tile, sbuf64);
     };
-    // block-Jacobi: the M^-1 copies of r, s (two, alternating like s), w and u
+    // block-Jacobi: the M^-1 copies of r, s (two, alternating like s), w and u,
+    // and for the replacement step's products those of t, y and the iterate
     VT* const RH = BJ ? (VT*)P.hat[0] : nullptr;
     VT* SHc = BJ ? (VT*)P.hat[1] : nullptr;
     VT* SHn = BJ ? (VT*)P.hat[2] : nullptr;
     VT* const WH = BJ ? (VT*)P.hat[3] : nullptr;
     VT* const UH = BJ ? (VT*)P.hat[4] : nullptr;
+    VT* const TH = BJ ? (VT*)P.hat[5] : nullptr;
+    VT* const YH = BJ ? (VT*)P.hat[6] : nullptr;
+    VT* const XH = BJ ? (VT*)P.hat[7] : nullptr;
     const VT* const BJE = (const VT*)P.bj;
     // (M^-1 v) on this lane's row, M^-1 stored [rows][bs] in block columns: the
     // block's values come from the lanes of the same block by shuffles and are
@@ -970,6 +974,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 // residual replacement iteration (Alg. 5)
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
                     const RowT row = (RowT)(tile * 32) + lane;
+                    VT u_out = VT(0);
                     if (row < n) {
                         const VT r = R[row], s = sCur[row], t = Tv[row], y = Y[row];
                         VT p = Pv[row], u = U[row];
@@ -978,13 +983,20 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         u = vfma(ze, o, et * vfma(be, u, y));
                         Pv[row] = p; O[row] = o; U[row] = u;
                         push(V_U, tile, row, u);
+                        u_out = u;
                     }
+                    if constexpr (BJ) {
+                        const VT h = bj_apply(BJE, u_out, row);
+                        if (row < n) UH[row] = h;
+                    }
+                    (void)u_out;
                 }
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // w_i = A u_i (q_i = A o_i is not used after a replacement); t, z, y_{i+1}, x_{i+1}
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                    const VT w = spmv(U, tile);
+                    const VT w = spmv(BJ ? UH : U, tile);
                     const RowT row = (RowT)(tile * 32) + lane;
+                    VT t_out = VT(0), y_out = VT(0), x_out = VT(0);
                     if (row < n) {
                         const VT o = O[row], r = R[row], u = U[row], s = sCur[row], y = Y[row], p = Pv[row];
                         VT z = Z[row], x = X[row];
@@ -996,15 +1008,23 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         push(xId, tile, row, x);
                         push(V_T, tile, row, t);
                         push(V_Y, tile, row, yn);
+                        t_out = t; y_out = yn; x_out = x;
                     }
+                    if constexpr (BJ) {
+                        const VT ht = bj_apply(BJE, t_out, row);
+                        const VT hy = bj_apply(BJE, y_out, row);
+                        const VT hx = bj_apply(BJE, x_out, row);
+                        if (row < n) { TH[row] = ht; YH[row] = hy; XH[row] = hx; }
+                    }
+                    (void)t_out; (void)y_out; (void)x_out;
                 }
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // r_{i+1} = b - A x_{i+1}; l_i = A t_i; g_{i+1} = A y_{i+1}
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                    const VT ax = spmv(X, tile);
-                    const VT at = spmv(Tv, tile);
-                    const VT ay = spmv(Y, tile);
+                    const VT ax = spmv(BJ ? XH : X, tile);
+                    const VT at = spmv(BJ ? TH : Tv, tile);
+                    const VT ay = spmv(BJ ? YH : Y, tile);
                     const RowT row = (RowT)(tile * 32) + lane;
                     VT qa_SB = VT(0), qb_SB = VT(0);
                     VT qa_SE = VT(0), qb_SE = VT(0);
@@ -1032,14 +1052,22 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     wa_acc(xv[SF], qa_SF, qb_SF, row < n);
                     wa_acc(xv[SH], qa_SH, qb_SH, row < n);
                     wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    if constexpr (BJ) {   // qa_SR = r_{i+1} on the lane's row (0 beyond n)
+                        const VT h = bj_apply(BJE, qa_SR, row);
+                        if (row < n) RH[row] = h;
+                    }
                 }
                 flush_partials<(1u << SB) | (1u << SE) | (1u << SF) | (1u << SH) | (1u << SR)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
                 // s_{i+1} = A r_{i+1}
                 wa_init10(xv);
                 for (int64_t tile = gwarp; tile < ntiles; tile += nwarps) {
-                    const VT s = spmv(R, tile);
+                    const VT s = spmv(BJ ? RH : R, tile);
                     const RowT row = (RowT)(tile * 32) + lane;
+                    if constexpr (BJ) {
+                        const VT h = bj_apply(BJE, s, row);
+                        if (row < n) SHn[row] = h;
+                    }
                     VT qa_SA = VT(0), qb_SA = VT(0);
                     VT qa_SC = VT(0), qb_SC = VT(0);
                     VT qa_SD = VT(0), qb_SD = VT(0);
@@ -1067,6 +1095,7 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                 ++rr_steps;
                 n_spmv += 5;  // w = A u; A x, A t, A y; s = A r
                 VT* tmp = sCur; sCur = sNxt; sNxt = tmp;
+                if constexpr (BJ) { VT* th = SHc; SHc = SHn; SHn = th; }
                 const int tid = sCurId; sCurId = sNxtId; sNxtId = tid;
             }
         }

@@ -72,20 +72,24 @@ def _gpu_solve(bcs, torch, A, b, kind, x0=None, **kw):
     return res, xd.cpu().numpy(), bcs.get_history(S), bcs.get_scalars(S)
 
 
-@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe"])
+@pytest.mark.parametrize("kind", ["ssBiCGSafe2", "p-BiCGSafe", "p-BiCGSafe-rr"])
 @pytest.mark.parametrize("name,bs,cfg", [("cd2d_64", 8, {}), ("cd2d_64", 1, {}), ("cd2d_64", 32, dict(max_ctas=3)),
                                          ("powerlaw_20001", 4, dict(max_ctas=16)),
                                          ("pivoting_203", 8, dict(max_ctas=1))])
 def test_bjacobi_solve_bit_identical(env, kind, name, bs, cfg):
-    """FP64: histories, scalars, iteration and outer-step counts and x bit-identical to the
-    oracle's preconditioned runs (several grid sizes, ragged n)."""
+    """FP64: histories, scalars, iteration, outer-step and replacement counts and x
+    bit-identical to the oracle's preconditioned runs (several grid sizes, ragged n; a
+    replacement every 10 iterations for p-BiCGSafe-rr)."""
     bcs, torch, orc = env
     A = MATS[name]()
     b = W.rhs_ones(A)
-    res, x, h, sc = _gpu_solve(bcs, torch, A, b, kind, block_size=bs, **cfg)
-    ref = orc.solve_bjacobi(A, b, bs, kind=kind, tol=1e-10, maxit=5000, max_restarts=29)
+    res, x, h, sc = _gpu_solve(bcs, torch, A, b, kind, block_size=bs, rr_m=10, **cfg)
+    ref = orc.solve_bjacobi(A, b, bs, kind=kind, tol=1e-10, maxit=5000, rr_m=10, max_restarts=29)
     assert res["status"] == 0 and ref["status"] == 0, (res, ref["status_name"])
     assert res["iterations"] == ref["iterations"]
+    assert res["rr_steps"] == ref["rr_steps"]
+    if kind == "p-BiCGSafe-rr":
+        assert res["rr_steps"] >= 1
     assert res["outer_steps"] == ref["restarts"] + 1
     assert np.array_equal(h, ref["hist"])
     assert np.array_equal(sc[:len(ref["scalars"])], ref["scalars"][:len(sc)])
@@ -129,8 +133,7 @@ def test_bjacobi_refusals(env):
     bcs, torch, orc = env
     A = W.cd2d(20, 20.0)
     M = bcs.csr_upload(A, layouts=bcs.LAYOUT_CSR | bcs.LAYOUT_SELL)
-    bad = [dict(kind="p-BiCGSafe-rr"), dict(layout="sell"), dict(threads_per_row=8), dict(tile_order=2),
-           dict(block_size=3), dict(block_size=64)]
+    bad = [dict(layout="sell"), dict(threads_per_row=8), dict(tile_order=2), dict(block_size=3), dict(block_size=64)]
     for kw in bad:
         kind = kw.pop("kind", "p-BiCGSafe")
         with pytest.raises(bcs.BcsError):
@@ -145,6 +148,22 @@ def test_bjacobi_refusals(env):
     S0 = bcs.solver_create(M, "p-BiCGSafe")
     with pytest.raises(bcs.BcsError):
         bcs.precond_blocks(S0)
+
+
+def test_bjacobi_rr_reaches_tolerance_where_pipelined_stalls(env):
+    """Blocks of 2 rows on the 128^3 system: p-BiCGSafe's recursive residual stalls above 1e-10
+    (the residual gap of Section 4); with replacement steps every 100 iterations p-BiCGSafe-rr
+    reaches the FP64 true residual of 1e-10."""
+    bcs, torch, orc = env
+    A = W.cd3d_upwind(128, 50.0)
+    b = W.rhs_ones(A)
+    M = bcs.csr_upload(A)
+    S = bcs.solver_create(M, "p-BiCGSafe-rr", tol=1e-10, maxit=10000, precond="block-jacobi", block_size=2)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    assert res["status"] == 0 and res["rr_steps"] >= 1, res
+    assert orc.true_residual(A, b, x.cpu().numpy()) / np.linalg.norm(b) <= 1e-10
 
 
 @pytest.mark.parametrize("bs", [2, 8])
