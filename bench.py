@@ -125,6 +125,8 @@ def args_parse():
     ap.add_argument("--precond", default="none", choices=["none", "jacobi", "block-jacobi"],
                     help="side workloads: preconditioner")
     ap.add_argument("--block-size", type=int, default=8, help="block-jacobi: rows per diagonal block")
+    ap.add_argument("--matrix", default=None,
+                    help="side measurement on a Matrix Market file (a supplied SuiteSparse matrix): b = A*1, x0 = 0")
     ap.add_argument("--big-ctas", type=int, default=-1,
                     help="batch: CTAs per cluster of the second lane for the largest systems (0 = one lane; "
                          "default: 8 with FP32/BF16 inner solves, where it was measured 10 %% faster, 0 in FP64, "
@@ -348,8 +350,11 @@ def reference_arm(a):
 
 def side_single(a, bcs, torch, dist, world, rank):
     import workloads as W
-    A = (W.powerlaw() if a.workload == "powerlaw_4m" else W.cd3d_upwind(128, 50.0) if a.workload == "cd3d_128_pc"
-         else W.cd3d27(192, 100.0))
+    if a.matrix:
+        A = W.read_matrix_market(a.matrix)
+    else:
+        A = (W.powerlaw() if a.workload == "powerlaw_4m" else W.cd3d_upwind(128, 50.0) if a.workload == "cd3d_128_pc"
+             else W.cd3d27(192, 100.0))
     b = W.rhs_ones(A)
     layouts = bcs.LAYOUT_CSR | bcs.LAYOUT_SELL
     M = bcs.csr_upload(A, layouts=layouts, stores=bcs.STORE_F32 | bcs.STORE_BF16)
@@ -394,7 +399,8 @@ def side_single(a, bcs, torch, dist, world, rank):
             "ms_per_solve": t * 1e3, "iterations": res["iterations"], "outer_steps": res["outer_steps"],
             "us_per_iter": t * 1e6 / max(1, res["iterations"]), "status": res["status_name"],
             "rel_res_true": res["rel_res_true"],
-            "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "n": A.n, "nnz": A.nnz,
+            "config": {"workload": ("Matrix Market file %s" % os.path.basename(a.matrix)) if a.matrix else
+                       "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "n": A.n, "nnz": A.nnz,
                        "kind": a.kind, "precision": a.precision, "layout": layout, "threads_per_row": tpr,
                        "precond": a.precond,
                        "block_size": a.block_size if a.precond == "block-jacobi" else None},
@@ -471,8 +477,8 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     import paper_2108_10591_gb300 as bcs
 
-    if a.workload != "cd3d_128":
-        fn = side_batch if a.workload == "batch_cd2d_512" else side_single
+    if a.workload != "cd3d_128" or a.matrix:
+        fn = side_batch if (a.workload == "batch_cd2d_512" and not a.matrix) else side_single
         line = fn(a, bcs, torch, dist, world, rank)
         if rank == 0:
             line["data"] = "synthetic"

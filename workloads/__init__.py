@@ -52,6 +52,55 @@ def rhs_ones(A: CSR) -> np.ndarray:
     return b
 
 
+def read_matrix_market(path: str) -> CSR:
+    """A square real matrix from a Matrix Market file (coordinate format; real, integer or
+    pattern; general, symmetric or skew-symmetric), as canonical CSR: columns ascending in
+    every row, repeated (row, column) entries summed.  Symmetric files list one triangle: the
+    mirrored entries are added (negated for skew-symmetric).  Pattern entries are 1.  This is
+    how a supplied SuiteSparse matrix (the paper's Table 2) enters the solvers; none ships with
+    this repository."""
+    with open(path) as fh:
+        header = fh.readline().split()
+        if len(header) < 5 or header[0] != "%%MatrixMarket" or header[1].lower() != "matrix":
+            raise ValueError("not a Matrix Market matrix file: %s" % path)
+        fmt, field, sym = header[2].lower(), header[3].lower(), header[4].lower()
+        if fmt != "coordinate":
+            raise ValueError("only the coordinate format is read (got %s)" % fmt)
+        if field not in ("real", "integer", "pattern"):
+            raise ValueError("only real, integer or pattern entries are read (got %s)" % field)
+        if sym not in ("general", "symmetric", "skew-symmetric"):
+            raise ValueError("only general, symmetric or skew-symmetric matrices are read (got %s)" % sym)
+        line = fh.readline()
+        while line.startswith("%") or not line.strip():
+            line = fh.readline()
+        m, ncols, nz = (int(t) for t in line.split()[:3])
+        if m != ncols:
+            raise ValueError("the solvers take square matrices (got %d x %d)" % (m, ncols))
+        ncolumns = 2 if field == "pattern" else 3
+        data = np.loadtxt(fh, ndmin=2, comments="%", usecols=range(ncolumns)) if nz else np.zeros((0, ncolumns))
+    if data.shape[0] != nz:
+        raise ValueError("expected %d entries, read %d" % (nz, data.shape[0]))
+    rows = data[:, 0].astype(np.int64) - 1
+    cols = data[:, 1].astype(np.int64) - 1
+    vals = np.ones(nz) if field == "pattern" else data[:, 2].astype(np.float64)
+    if nz and (rows.min() < 0 or cols.min() < 0 or rows.max() >= m or cols.max() >= m):
+        raise ValueError("entry index out of range")
+    if sym != "general":
+        off = rows != cols
+        sign = -1.0 if sym == "skew-symmetric" else 1.0
+        rows, cols, vals = (np.concatenate([rows, cols[off]]), np.concatenate([cols, rows[off]]),
+                            np.concatenate([vals, sign * vals[off]]))
+    key = rows * m + cols
+    uk, inv = np.unique(key, return_inverse=True)
+    summed = np.zeros(len(uk))
+    np.add.at(summed, inv, vals)
+    r, c = uk // m, uk % m
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    np.cumsum(rowptr, out=rowptr)
+    return CSR(m, rowptr, c.astype(np.int32), summed)
+
+
 def _stencil(dims, offsets):
     """Assemble a stencil matrix on a lexicographic grid (x fastest).
     dims: (kx, ky[, kz]); offsets: list of (offset tuple, coefficient)."""
