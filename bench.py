@@ -481,7 +481,7 @@ def main():
         fn = side_batch if (a.workload == "batch_cd2d_512" and not a.matrix) else side_single
         line = fn(a, bcs, torch, dist, world, rank)
         if rank == 0:
-            line["data"] = "synthetic"
+            line["data"] = "matrix file" if a.matrix else "synthetic"
             line["side_measurement"] = True
             print(json.dumps(line), flush=True)
         if dist:
