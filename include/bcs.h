@@ -70,8 +70,9 @@ enum { BCS_LAYOUT_AUTO = 0, BCS_LAYOUT_CSR = 1, BCS_LAYOUT_SELL = 2 };
  * multiplies by A is also written as M^-1 v by the same pass that writes v
  * (the blocks lie inside the solver's 32-row tiles, so this needs no extra
  * barrier), and the products gather that copy.  Single-system solves with
- * CSR, one lane per row and the static tile order (the defaults are adjusted;
- * an explicit other choice is BCS_ERR_ARG), all three kinds (the replacement
+ * CSR, one lane per row and the static tile order (the defaults, including
+ * BCS_LAYOUT_AUTO on a matrix tuned to SELL, are adjusted; an explicit other
+ * choice is BCS_ERR_ARG), all three kinds (the replacement
  * steps of BCS_P_BICGSAFE_RR form the copies of u, t, y, x and r they
  * multiply). */
 enum { BCS_PRECOND_NONE = 0, BCS_PRECOND_JACOBI = 1, BCS_PRECOND_BLOCK_JACOBI = 2 };

@@ -195,12 +195,13 @@ int bcs_solver_create(bcs_matrix A, int kind, double tol, int maxit, const bcs_o
     if (o.rr_M == 0) o.rr_M = maxit < INT_MAX ? maxit + 1 : maxit;  // 0 = no limit below maxit
     int rc = check_options(o);
     if (rc) return rc;
+    const bool bj = o.precond == BCS_PRECOND_BLOCK_JACOBI;
     if (o.layout == BCS_LAYOUT_AUTO) {
-        const int tl = A->tuned_layout[o.precision];
+        // block-Jacobi runs on CSR whatever layout the matrix was tuned to
+        const int tl = bj ? 0 : A->tuned_layout[o.precision];
         o.layout = (tl && (A->layouts & tl)) ? tl : BCS_LAYOUT_CSR;
     }
     if (!(A->layouts & o.layout)) return BCS_ERR_ARG;
-    const bool bj = o.precond == BCS_PRECOND_BLOCK_JACOBI;
     if (bj) {
         // built for CSR with one lane per row in the static tile order
         if (o.layout != BCS_LAYOUT_CSR || (o.threads_per_row != 0 && o.threads_per_row != 1) || o.tile_order == 2)

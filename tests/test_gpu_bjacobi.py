@@ -140,6 +140,11 @@ def test_bjacobi_refusals(env):
             bcs.solver_create(M, kind, precond="block-jacobi", **kw)
     S = bcs.solver_create(M, "p-BiCGSafe", precond="block-jacobi", threads_per_row=1, tile_order=1)
     assert bcs.precond_blocks(S)[0].shape == (A.n, 8)   # default block size 8
+    # after autotuning (which may record SELL for the matrix) the default layout still gives a
+    # block-Jacobi solver on CSR
+    bcs.autotune(M, "p-BiCGSafe", precision="fp64", iters=5)
+    S = bcs.solver_create(M, "p-BiCGSafe", precond="block-jacobi", layout="auto")
+    assert bcs.precond_blocks(S)[0].shape == (A.n, 8)
     Ad = np.eye(16)
     Ad[2:4, 2:4] = [[1.0, 2.0], [2.0, 4.0]]
     Ad[3, 9] = 1.0
