@@ -97,6 +97,20 @@ def test_bjacobi_solve_bit_identical(env, kind, name, bs, cfg):
     assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
 
 
+@pytest.mark.parametrize("n,bs", [(1, 8), (5, 8), (33, 4), (37, 32)])
+def test_bjacobi_tiny_and_ragged(env, n, bs):
+    """Systems smaller than one block or one tile, and a last block of one row: bit-identical to
+    the oracle (a single ragged block is the whole matrix: its M^-1 is the inverse)."""
+    bcs, torch, orc = env
+    A = W.tiny_random(n, seed=n, density=0.5) if n > 1 else W.dense_to_csr(np.array([[3.0]]))
+    b = W.rhs_ones(A)
+    res, x, h, sc = _gpu_solve(bcs, torch, A, b, "p-BiCGSafe", block_size=bs, maxit=500)
+    ref = orc.solve_bjacobi(A, b, bs, kind="p-BiCGSafe", tol=1e-10, maxit=500, max_restarts=29)
+    assert res["status"] == ref["status"] == 0, (res, ref["status_name"])
+    assert res["iterations"] == ref["iterations"]
+    assert np.array_equal(h, ref["hist"]) and np.array_equal(x, ref["x"])
+
+
 def test_bjacobi_start_vector(env):
     """A non-zero x_0 enters as y_0 = M x_0 on both sides: bit-identical runs."""
     bcs, torch, orc = env
