@@ -97,3 +97,18 @@ def test_host_tensors_are_refused_before_the_library(bcs):
         bcs.dot(x, x)
     with pytest.raises(ValueError, match="CUDA tensor"):
         bcs.dot_noalloc(x, x, torch.zeros(1, dtype=torch.float64))
+
+
+def test_import_fails_loudly_without_the_library(tmp_path):
+    """The binding has no CPU fallback: a package directory without libbcs.so refuses to
+    import, naming the missing library."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2108_10591_gb300"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2108_10591_gb300", "__init__.py"), pkg / "__init__.py")
+    r = subprocess.run([sys.executable, "-c", "import paper_2108_10591_gb300"], cwd=str(tmp_path),
+                       capture_output=True, text=True, env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libbcs.so is not built" in r.stderr
