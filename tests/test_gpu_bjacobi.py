@@ -221,3 +221,41 @@ def test_bjacobi_cd3d_128(env, prec):
     x = xd.cpu().numpy()
     assert res["status"] == 0, res
     assert orc.true_residual(A, b, x) / np.linalg.norm(b) <= 1e-10
+
+
+def _golden_bjacobi():
+    import json
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cd3d128_bjacobi_solves.json")
+    with open(p) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("key", ["p-BiCGSafe/4", "p-BiCGSafe-rr/2", "ssBiCGSafe2/8"])
+def test_bjacobi_cd3d_128_full_solve_matches_oracle(env, key):
+    """The complete preconditioned FP64 solves of the 128^3 system in the default launch
+    configuration against the oracle's (tests/golden/cd3d128_bjacobi_solves.json, written by
+    make_cd3d128_bjacobi_solves.py from oracle/ alone): the same iterations, outer runs and
+    replacement steps, the same true residual and the same x, bit for bit."""
+    import hashlib
+    bcs, torch, orc = env
+    gold = _golden_bjacobi()
+    g = gold["solves"][key]
+    o = gold["options"]
+    A = W.cd3d_upwind(128, 50.0)
+    b = W.rhs_ones(A)
+    assert hashlib.sha256(np.ascontiguousarray(b, dtype="<f8").tobytes()).hexdigest() == gold["b_sha256"]
+    M = bcs.csr_upload(A)
+    S = bcs.solver_create(M, g["kind"], tol=o["tol"], maxit=o["maxit"], max_outer=o["max_runs"], rr_m=o["rr_m"],
+                          rr_M=o["rr_M"], precond="block-jacobi", block_size=g["block_size"])
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    assert g["status"] == "ok" and res["status"] == bcs.OK
+    assert res["iterations"] == g["iterations"]
+    assert res["outer_steps"] == g["outer_steps"] and res["rr_steps"] == g["rr_steps"]
+    xh = x.cpu().numpy()
+    rows = np.asarray(gold["sample_rows"])
+    assert np.array_equal(xh[rows], np.array([float.fromhex(v) for v in g["x_sample"]]))
+    assert hashlib.sha256(np.ascontiguousarray(xh, dtype="<f8").tobytes()).hexdigest() == g["x_sha256"]
+    assert res["rel_res_true"] == float.fromhex(g["rel_res_true"])
