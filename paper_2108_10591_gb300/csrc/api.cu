@@ -328,6 +328,15 @@ static void fill_params(bcs_solver s, const double* b, double* x, KParams* P) {
     P->scal = s->scal;
     P->out = s->out;
     P->l2hint = s->l2hint;
+    // FP64 with one lane per CSR row or SELL in the static order: when every warp
+    // adds at most 64 products per lane (one per tile it takes), the kernel that
+    // places the inner-product terms 12 bits higher in their windows (wa_acc
+    // shift 14, room for 2^7 terms) drops 12 fewer low bits of the smaller terms
+    {
+        const int64_t warps = (int64_t)s->grid * kSolveWarps;
+        P->wa_hi = (!s->vt_f32 && !s->dyn && !s->bj_bs && s->tpr == 1 &&
+                    (P->ntiles + warps - 1) / warps <= 64) ? 1 : 0;
+    }
     if (s->bj_bs) {
         P->bs = s->bj_bs;
         P->bj64 = s->bjE;

@@ -72,6 +72,8 @@ struct KParams {
     double* scal;           // [4*hist_cap]
     double* out;            // [NOUT]
     int l2hint;             // launch the L2-hinted kernel (FP32 vectors, CSR, one lane per row; see l2_hint_pays)
+    int wa_hi;              // FP64, static order: the kernel whose inner-product terms sit 12 bits higher
+                            // (wa_acc shift 14; at most 64 products per lane)
     // block-Jacobi right preconditioning (bs = 0: none): M^-1 in the inner
     // value type and in FP64, [rows][bs] in block columns (rows padded to
     // whole tiles, zero there); the M^-1 copies of r, s, s2, w, u, t, y and the

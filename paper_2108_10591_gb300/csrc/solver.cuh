@@ -226,8 +226,10 @@ struct ClusterGroup {
 // the products gather those copies.  The solved system's iterate y is x64;
 // the caller turns x = M^-1 y after the launch (CSR, one lane per row, static
 // tile order; all three kinds).
+// HI: FP64 inner-product terms placed 12 bits higher in their windows (wa_acc
+// shift 14 instead of 2), for solves whose warps add at most 64 products per lane.
 template <class VT, class MT, int LAYOUT, int T, int NW, bool DYN, class Group, bool DIST = false, bool H = false,
-          bool BJ = false>
+          bool BJ = false, bool HI = false>
 __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     __shared__ XStage<NW> s_x;
     __shared__ double s_sum[10];
@@ -275,6 +277,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     const VT* const Bin = mixed ? (const VT*)BinW : (const VT*)(const void*)P.b64;
     const int xId = mixed ? (int)V_D : (int)NVEC;
     const MT* const val = (const MT*)P.val;
+    // left shift of the FP64 products in the exact inner-product windows (wa_acc)
+    constexpr int was = HI ? 14 : 2;
     // row index inside a tile loop: 32-bit with FP32 vectors (fewer address
     // instructions per tile, measured faster); 64-bit with FP64 vectors, where
     // the 32-bit form was measured slower.  n < 2^31 (checked at upload).
@@ -508,8 +512,8 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     const VT h = bj_apply(BJE, qa_SF, row);
                     if (row < n) RH[row] = h;
                 }
-                wa_acc(xt[ST], qa_ST, qb_ST, row < n);
-                wa_acc(xv[SF], qa_SF, qb_SF, row < n);
+                wa_acc(xt[ST], qa_ST, qb_ST, row < n, was);
+                wa_acc(xv[SF], qa_SF, qb_SF, row < n, was);
             }
             xv[SR] = xv[SF];
             flush_partials<(1u << SF) | (1u << SR), (1u << SB) | (1u << SC) | (1u << SE) | (1u << SH)>(xv, s_x,
@@ -561,9 +565,9 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                     qa_SG = rsv;
                     qb_SG = sv;
                 }
-                wa_acc(xv[SA], qa_SA, qb_SA, row < n);
-                wa_acc(xv[SD], qa_SD, qb_SD, row < n);
-                wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                wa_acc(xv[SA], qa_SA, qb_SA, row < n, was);
+                wa_acc(xv[SD], qa_SD, qb_SD, row < n, was);
+                wa_acc(xv[SG], qa_SG, qb_SG, row < n, was);
             }
             flush_partials<(1u << SA) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(0));
             if (!grp.sync(&s_flag)) { stg.settle(); return; }
@@ -615,10 +619,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         qa_SG = rsv;
                         qb_SG = sv;
                     }
-                    wa_acc(xv[SA], qa_SA, qb_SA, row < n);
-                    wa_acc(xv[SC], qa_SC, qb_SC, row < n);
-                    wa_acc(xv[SD], qa_SD, qb_SD, row < n);
-                    wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                    wa_acc(xv[SA], qa_SA, qb_SA, row < n, was);
+                    wa_acc(xv[SC], qa_SC, qb_SC, row < n, was);
+                    wa_acc(xv[SD], qa_SD, qb_SD, row < n, was);
+                    wa_acc(xv[SG], qa_SG, qb_SG, row < n, was);
                     stage_at(FirstPA{}, vPA, t2, kt);
                     t0 = t1;
                     t1 = t2;
@@ -822,11 +826,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         qa_SR = rn;
                         qb_SR = rn;
                     }
-                    wa_acc(xv[SB], qa_SB, qb_SB, row < n);
-                    wa_acc(xv[SE], qa_SE, qb_SE, row < n);
-                    wa_acc(xv[SF], qa_SF, qb_SF, row < n);
-                    wa_acc(xv[SH], qa_SH, qb_SH, row < n);
-                    wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    wa_acc(xv[SB], qa_SB, qb_SB, row < n, was);
+                    wa_acc(xv[SE], qa_SE, qb_SE, row < n, was);
+                    wa_acc(xv[SF], qa_SF, qb_SF, row < n, was);
+                    wa_acc(xv[SH], qa_SH, qb_SH, row < n, was);
+                    wa_acc(xv[SR], qa_SR, qb_SR, row < n, was);
                     if constexpr (BJ) {   // qa_SR = r_{i+1} on the lane's row (0 beyond n)
                         const VT h = bj_apply(BJE, qa_SR, row);
                         if (row < n) RH[row] = h;
@@ -891,11 +895,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         qa_SR = rn;
                         qb_SR = rn;
                     }
-                    wa_acc(xv[SB], qa_SB, qb_SB, row < n);
-                    wa_acc(xv[SE], qa_SE, qb_SE, row < n);
-                    wa_acc(xv[SF], qa_SF, qb_SF, row < n);
-                    wa_acc(xv[SH], qa_SH, qb_SH, row < n);
-                    wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    wa_acc(xv[SB], qa_SB, qb_SB, row < n, was);
+                    wa_acc(xv[SE], qa_SE, qb_SE, row < n, was);
+                    wa_acc(xv[SF], qa_SF, qb_SF, row < n, was);
+                    wa_acc(xv[SH], qa_SH, qb_SH, row < n, was);
+                    wa_acc(xv[SR], qa_SR, qb_SR, row < n, was);
                     if constexpr (BJ) {
                         const VT h = bj_apply(BJE, w_out, row);
                         if (row < n) WH[row] = h;
@@ -953,10 +957,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         qa_SG = rs;
                         qb_SG = s;
                     }
-                    wa_acc(xv[SA], qa_SA, qb_SA, row < n);
-                    wa_acc(xv[SC], qa_SC, qb_SC, row < n);
-                    wa_acc(xv[SD], qa_SD, qb_SD, row < n);
-                    wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                    wa_acc(xv[SA], qa_SA, qb_SA, row < n, was);
+                    wa_acc(xv[SC], qa_SC, qb_SC, row < n, was);
+                    wa_acc(xv[SD], qa_SD, qb_SD, row < n, was);
+                    wa_acc(xv[SG], qa_SG, qb_SG, row < n, was);
                     if constexpr (BJ) {   // qa_SA = s_{i+1} on the lane's row (0 beyond n)
                         const VT h = bj_apply(BJE, qa_SA, row);
                         if (row < n) SHn[row] = h;
@@ -1047,11 +1051,11 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         qa_SR = rn;
                         qb_SR = rn;
                     }
-                    wa_acc(xv[SB], qa_SB, qb_SB, row < n);
-                    wa_acc(xv[SE], qa_SE, qb_SE, row < n);
-                    wa_acc(xv[SF], qa_SF, qb_SF, row < n);
-                    wa_acc(xv[SH], qa_SH, qb_SH, row < n);
-                    wa_acc(xv[SR], qa_SR, qb_SR, row < n);
+                    wa_acc(xv[SB], qa_SB, qb_SB, row < n, was);
+                    wa_acc(xv[SE], qa_SE, qb_SE, row < n, was);
+                    wa_acc(xv[SF], qa_SF, qb_SF, row < n, was);
+                    wa_acc(xv[SH], qa_SH, qb_SH, row < n, was);
+                    wa_acc(xv[SR], qa_SR, qb_SR, row < n, was);
                     if constexpr (BJ) {   // qa_SR = r_{i+1} on the lane's row (0 beyond n)
                         const VT h = bj_apply(BJE, qa_SR, row);
                         if (row < n) RH[row] = h;
@@ -1085,10 +1089,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
                         qa_SG = rs;
                         qb_SG = s;
                     }
-                    wa_acc(xv[SA], qa_SA, qb_SA, row < n);
-                    wa_acc(xv[SC], qa_SC, qb_SC, row < n);
-                    wa_acc(xv[SD], qa_SD, qb_SD, row < n);
-                    wa_acc(xv[SG], qa_SG, qb_SG, row < n);
+                    wa_acc(xv[SA], qa_SA, qb_SA, row < n, was);
+                    wa_acc(xv[SC], qa_SC, qb_SC, row < n, was);
+                    wa_acc(xv[SD], qa_SD, qb_SD, row < n, was);
+                    wa_acc(xv[SG], qa_SG, qb_SG, row < n, was);
                 }
                 flush_partials<(1u << SA) | (1u << SC) | (1u << SD) | (1u << SG)>(xv, s_x, myrec(nxt));
                 if (!grp.sync(&s_flag)) { stg.settle(); return; }
@@ -1144,10 +1148,10 @@ __device__ __forceinline__ void solve_body(const KParams& P, Group& grp) {
     }
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false, bool BJ = false>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false, bool BJ = false, bool HI = false>
 __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(const __grid_constant__ KParams P) {
     GridGroup grp{GridBarrier{P.bar, P.err, gridDim.x, 0u, P.spin_budget}, (int)blockIdx.x, (int)gridDim.x};
-    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN, GridGroup, false, H, BJ>(P, grp);
+    solve_body<VT, MT, LAYOUT, T, kSolveWarps, DYN, GridGroup, false, H, BJ, HI>(P, grp);
 }
 
 // Partitioned solve (bcs_dist.h): one cooperative launch whose CTAs are split
@@ -1181,14 +1185,14 @@ constexpr size_t stage_smem_bytes() {
     return (size_t)NW * 2 * kMaxStage * 32 * sizeof(VT);
 }
 
-template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false, bool BJ = false>
+template <class VT, class MT, int LAYOUT, int T, bool DYN, bool H = false, bool BJ = false, bool HI = false>
 int launch_one(const KParams& P, int grid, cudaStream_t st) {
     void* args[] = {(void*)&P};
     const size_t smem = stage_smem_bytes<VT, kSolveWarps>();
-    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H, BJ>,
+    cudaError_t e = cudaFuncSetAttribute((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H, BJ, HI>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H, BJ>, dim3(grid),
+    return (int)cudaLaunchCooperativeKernel((const void*)solve_kernel<VT, MT, LAYOUT, T, DYN, H, BJ, HI>, dim3(grid),
                                             dim3(kSolveBlock), args, smem, st);
 }
 
@@ -1241,6 +1245,12 @@ int dispatch(const KParams* P, int layout, int tpr, int grid, cudaStream_t st, i
 #define BCS_CASE(LAY, TT, D)                                                              \
     return P ? launch_one<VT, MT, LAY, TT, D>(*P, grid, st) : max_grid_one<VT, MT, LAY, TT, D>(max_grid)
     if constexpr (SUBSET == 0) {
+        if constexpr (sizeof(VT) == 8) {   // FP64 with the higher inner-product placement
+            if (P && P->wa_hi) {
+                if (layout == LAY_SELL) return launch_one<VT, MT, LAY_SELL, 1, false, false, false, true>(*P, grid, st);
+                return launch_one<VT, MT, LAY_CSR, 1, false, false, false, true>(*P, grid, st);
+            }
+        }
         if (layout == LAY_SELL) { BCS_CASE(LAY_SELL, 1, false); }
         if constexpr (sizeof(VT) == 4) {   // CSR, one lane per row, with the L2 hints
             if (P && P->l2hint) return launch_one<VT, MT, LAY_CSR, 1, false, true>(*P, grid, st);

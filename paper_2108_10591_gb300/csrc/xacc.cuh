@@ -278,8 +278,14 @@ __device__ __forceinline__ void wa_add_term(WAcc& a, unsigned long long ph, unsi
     xa_add128(a.hi, a.lo, ph, pl);
 }
 
-// x * y, FP64 operands: exact 106-bit product, placed with its top at bit 108.
-__device__ __forceinline__ void wa_acc(WAcc& a, double x, double y, bool valid) {
+// x * y, FP64 operands: the exact 106-bit product shifted left by s (2 <= s <=
+// 20), so that the warp's largest term fills bits up to 105 + s of the window
+// and the window's bottom lies 105 + s bits below that term's top.  A lane adds
+// k terms below 2^(106 + s), so its 128-bit sum cannot overflow while
+// k <= 2^(21 - s); the solver picks the largest s its tiles per warp allow (the
+// larger s, the fewer low bits of the smaller terms are dropped), s = 2 holds
+// for up to 2^19 terms.
+__device__ __forceinline__ void wa_acc(WAcc& a, double x, double y, bool valid, int s = 2) {
     const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
     const unsigned long long by = (unsigned long long)__double_as_longlong(y);
     const int Ex = (int)((bx >> 52) & 0x7FF), Ey = (int)((by >> 52) & 0x7FF);
@@ -288,12 +294,12 @@ __device__ __forceinline__ void wa_acc(WAcc& a, double x, double y, bool valid) 
     unsigned long long my = (by & 0xFFFFFFFFFFFFFull) | (Ey ? (1ull << 52) : 0ull);
     const bool live = valid && !special && mx != 0ull && my != 0ull;
     const unsigned long long ph = __umul64hi(mx, my), pl = mx * my;
-    const int pe = (Ex ? Ex - 1075 : -1074) + (Ey ? Ey - 1075 : -1074) - 2;
-    wa_add_term(a, (ph << 2) | (pl >> 62), pl << 2, pe, ((bx ^ by) >> 63) != 0ull, live, special);
+    const int pe = (Ex ? Ex - 1075 : -1074) + (Ey ? Ey - 1075 : -1074) - s;
+    wa_add_term(a, (ph << s) | (pl >> (64 - s)), pl << s, pe, ((bx ^ by) >> 63) != 0ull, live, special);
 }
 
 // x * y, FP32 operands: exact 48-bit product, placed with its top at bit 108.
-__device__ __forceinline__ void wa_acc(WAcc& a, float x, float y, bool valid) {
+__device__ __forceinline__ void wa_acc(WAcc& a, float x, float y, bool valid, int = 2) {
     const unsigned bx = __float_as_uint(x), by = __float_as_uint(y);
     const int Ex = (int)((bx >> 23) & 0xFF), Ey = (int)((by >> 23) & 0xFF);
     const bool special = valid && (Ex == 0xFF || Ey == 0xFF);
@@ -363,7 +369,7 @@ __device__ __forceinline__ void wa_init(DAcc& a) { a.s = 0.0; }
 // instructions per tile).  A pure function of its operand, so the widening of
 // a value that enters several inner products is computed once.
 __device__ __forceinline__ double widen(float f) { return (double)f; }
-__device__ __forceinline__ void wa_acc(DAcc& a, float x, float y, bool valid) {
+__device__ __forceinline__ void wa_acc(DAcc& a, float x, float y, bool valid, int = 2) {
     if (valid) a.s = fma(widen(x), widen(y), a.s);
 }
 

@@ -196,6 +196,38 @@ def test_cd3d27_192_spmv_all_stores(env, cd3d27):
             assert np.all(np.abs(y - exact) <= bound + 1e-30), (store, lay, tpr)
 
 
+GOLDEN27 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cd3d27_192_full_solves.json")
+
+
+@pytest.mark.parametrize("kind,layout", [("ssBiCGSafe2", "csr"), ("p-BiCGSafe-rr", "csr"), ("ssBiCGSafe2", "sell")])
+def test_cd3d27_192_full_solve_matches_oracle(env, cd3d27, kind, layout):
+    """The complete FP64 solves of the 27-point system (n = 7,077,888) against the oracle's
+    (tests/golden/cd3d27_192_full_solves.json, written by make_cd3d27_192_full_solves.py from
+    oracle/ alone), CSR with one lane per row and SELL-32-256: the same iterations, outer runs
+    and replacement steps, the same true residual and x, bit for bit."""
+    bcs, torch, orc = env
+    A, M = cd3d27
+    b = W.rhs_ones(A)
+    with open(GOLDEN27) as fh:
+        gold = json.load(fh)
+    assert _sha(b) == gold["b_sha256"]
+    o = gold["options"]
+    g = gold["solves"][kind]
+    S = bcs.solver_create(M, kind, tol=o["tol"], maxit=o["maxit"], max_outer=o["max_runs"], rr_m=o["rr_m"],
+                          rr_M=o["rr_M"], layout=layout, threads_per_row=1 if layout == "csr" else 0)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    assert g["status"] == "ok" and res["status"] == bcs.OK
+    assert res["iterations"] == g["iterations"]
+    assert res["outer_steps"] == g["outer_steps"] and res["rr_steps"] == g["rr_steps"]
+    xh = x.cpu().numpy()
+    rows = np.asarray(gold["sample_rows"])
+    assert np.array_equal(xh[rows], np.array([float.fromhex(v) for v in g["x_sample"]]))
+    assert _sha(xh) == g["x_sha256"]
+    assert res["rel_res_true"] == float.fromhex(g["rel_res_true"])
+
+
 @pytest.mark.parametrize("kind,prec,layout", [("p-BiCGSafe", "fp32", "csr"), ("p-BiCGSafe", "fp32", "sell"),
                                               ("p-BiCGSafe-rr", "fp64", "csr"), ("ssBiCGSafe2", "fp64", "sell")])
 def test_cd3d27_192_full_solve_true_residual(env, cd3d27, kind, prec, layout):
