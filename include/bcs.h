@@ -213,9 +213,10 @@ int bcs_spmv(bcs_matrix A, int layout, int store, const void* x, void* y, int ve
  * computes them.  Each product is formed exactly as an integer and
  * accumulated in 128-bit fixed point on the integer units; the sum is rounded
  * once to nearest even, so the result does not depend on the order of the
- * terms or the launch configuration (bits more than 2^-110 below the largest
- * term are dropped, which changes the result only when the sum cancels by a
- * factor of more than about 2^50).
+ * terms or the launch configuration.  Bits more than about 2^-107 below the
+ * largest product are dropped; they add up to at most n 2^-107 of it, so the
+ * result is the correctly rounded one unless |(x, y)| falls below about
+ * n 2^-54 times the largest |x_i y_i| (a cancellation of 2^34 for n = 10^6).
  *   n        number of elements (>= 0).
  *   x, y     device vectors, FP64 when vec_f32 == 0, FP32 otherwise.
  *   result   host double receiving the value (a NaN or Inf operand gives NaN).
@@ -233,10 +234,10 @@ int bcs_dot(int64_t n, const void* x, const void* y, int vec_f32, double* result
  * bcs_dot's kernels, but the per-CTA partial sums go to a fixed 128 KiB array
  * that the library holds on every GPU that loads it until the process exits
  * (at most 256 CTAs).  The value is the correctly rounded (x, y), as bcs_dot's
- * is, unless the sum cancels by more than about 2^50 relative to its largest
- * product: each lane's window drops bits more than 2^-108 below its largest
- * term, and the two calls give the terms to different numbers of CTAs, so
- * under such cancellation their last bits may differ.
+ * is, unless the sum cancels below about n 2^-54 of its largest product (see
+ * bcs_dot): the dropped bits depend on how the terms are split over CTAs, and
+ * the two calls split them differently, so under such cancellation their last
+ * bits may differ.
  *   n           number of elements, 0 <= n <= 2^33 (BCS_ERR_ARG beyond that).
  *   x, y        device vectors, FP64 when vec_f32 == 0, FP32 otherwise.
  *   result_dev  device double receiving the value; written asynchronously on

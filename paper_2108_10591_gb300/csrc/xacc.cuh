@@ -4,16 +4,18 @@
 // for FP64 operands, 24 x 24 -> 48 bits for FP32) with a power-of-two weight,
 // and added into a 128-bit two's-complement fixed-point window
 //     value = w * 2^e.
-// The window is anchored so that the largest term seen so far ends at bit
-// kTop (18 bits of headroom above it); when a larger term arrives the window
-// slides up, dropping bits more than 2^-110 below the largest term.  Partial
-// accumulators from different threads and CTAs are aligned to the larger
-// anchor and added as integers.  The final value is rounded once to FP64,
-// nearest even.  Up to the dropped bits (2^-110 relative to the largest term,
-// far below the 2^-53 rounding unit unless the sum cancels by more than ~2^50)
-// the result is the correctly rounded inner product, independent of the order
-// in which terms and partials were combined.  No FP64 arithmetic is used, so
-// the scarce FP64 units of the GPU stay with the recurrences and the SpMV.
+// The window is anchored so that the largest term seen so far fills its upper
+// bits, with headroom above for the carries of the terms a lane adds; when a
+// larger term arrives the window slides up.  Bits below the window's bottom
+// (about 2^-107 of the warp's largest term, 2^-119 with the high placement of
+// wa_acc) are dropped.  Partial accumulators from different threads and CTAs
+// are aligned to the larger anchor and added as integers, and the final value
+// is rounded once to FP64, nearest even.  The dropped bits add up to at most n
+// times the bottom's weight, so the result is the correctly rounded inner
+// product, independent of the order in which terms and partials were
+// combined, unless the sum cancels below about n 2^-54 (n 2^-66) of its
+// largest term.  No FP64 arithmetic is used, so the scarce FP64 units of the
+// GPU stay with the recurrences and the SpMV.
 #pragma once
 #include <stdint.h>
 
