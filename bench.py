@@ -38,9 +38,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "cd3d128_full_solves.json")
 # workload, p-BiCGSafe, CSR: captures of 10- and 20-iteration solves, differenced for the bytes of one
 # iteration; the intercept is the set-up and final true-residual work of an outer step.  Valid only
 # for the kernel sources they were taken on (KERNEL_SHA); otherwise the bench reports null.
-TRAFFIC = {"fp64": {"per_iter": 914.5e6, "per_outer": 1021.5e6},
-           "fp32": {"per_iter": 381.4e6, "per_outer": 872.8e6}}
-KERNEL_SHA = "4df873533bd4b0b4"
+TRAFFIC = {"fp64": {"per_iter": 914.4e6, "per_outer": 1021.8e6},
+           "fp32": {"per_iter": 381.3e6, "per_outer": 867.4e6}}
+KERNEL_SHA = "37789c66f04d6fdc"
 
 
 # The measured kernel's sources and its launch path.  Other translation units
