@@ -1,9 +1,12 @@
 """Parity at the full sizes of the synthetic configurations, in the launch
 configuration bench.py times (default options: one 24-warp CTA per SM, CSR one
 lane per row).  The oracle cannot finish these solves in seconds, so the checks
-are (a) the first 20 iterations, which the oracle can run, and (b) properties
-that hold at any size, measured by the oracle on the GPU's output: the FP64
-true residual ||b - A x|| / ||b|| <= 1e-10 at exit.
+are (a) the first 20 iterations, which the oracle can run; (b) the complete
+FP64 solves against golden files that scripts beside them wrote from oracle/
+alone (tests/golden/make_*_full_solves.py): the same iterations, outer runs,
+replacement steps, true residual and x, bit for bit; and (c) properties that
+hold at any size, measured by the oracle on the GPU's output: the FP64 true
+residual ||b - A x|| / ||b|| <= 1e-10 at exit.
 """
 import hashlib
 import json
@@ -113,13 +116,56 @@ def test_cd3d_128_full_solve_true_residual(env, cd3d, kind, prec):
     assert abs(rel - res["rel_res_true"]) <= 1e-3 * rel + 1e-16
 
 
-def test_powerlaw_4m_fp32_refinement(env):
+@pytest.fixture(scope="module")
+def powerlaw(env):
+    bcs, torch, orc = env
+    A = W.powerlaw()
+    M = bcs.csr_upload(A, stores=bcs.STORE_F32)
+    return A, M
+
+
+GOLDENPL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "powerlaw_4m_full_solves.json")
+PL_KINDS = ["ssBiCGSafe2", "p-BiCGSafe", "p-BiCGSafe-rr"]
+
+
+@pytest.mark.parametrize("tile_order", ["library", "static"])
+@pytest.mark.parametrize("kind", PL_KINDS)
+def test_powerlaw_4m_full_solve_matches_oracle(env, powerlaw, kind, tile_order):
+    """The complete FP64 solves of the irregular 4M-row system against the oracle's
+    (tests/golden/powerlaw_4m_full_solves.json, written by make_powerlaw_4m_full_solves.py
+    from oracle/ alone), CSR with one lane per row: in the library's tile order for this
+    matrix (warps claim tiles, as bench.py runs it) and in the static order, the same
+    iterations, outer runs and replacement steps, the same true residual and x, bit for bit."""
+    bcs, torch, orc = env
+    A, M = powerlaw
+    b = W.rhs_ones(A)
+    with open(GOLDENPL) as fh:
+        gold = json.load(fh)
+    assert _sha(b) == gold["b_sha256"]
+    o = gold["options"]
+    g = gold["solves"][kind]
+    S = bcs.solver_create(M, kind, tol=o["tol"], maxit=o["maxit"], max_outer=o["max_runs"], rr_m=o["rr_m"],
+                          rr_M=o["rr_M"], layout="csr", threads_per_row=1,
+                          tile_order=0 if tile_order == "library" else 1)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    res = bcs.solve(S, bd, x)
+    assert g["status"] == "ok" and res["status"] == bcs.OK
+    assert res["iterations"] == g["iterations"]
+    assert res["outer_steps"] == g["outer_steps"] and res["rr_steps"] == g["rr_steps"]
+    xh = x.cpu().numpy()
+    rows = np.asarray(gold["sample_rows"])
+    assert np.array_equal(xh[rows], np.array([float.fromhex(v) for v in g["x_sample"]]))
+    assert _sha(xh) == g["x_sha256"]
+    assert res["rel_res_true"] == float.fromhex(g["rel_res_true"])
+
+
+def test_powerlaw_4m_fp32_refinement(env, powerlaw):
     """The irregular 4M-row configuration (power-law rows up to 512): FP32 values and vectors
     with FP64 refinement reach the FP64 tolerance, checked by the oracle's true residual."""
     bcs, torch, orc = env
-    A = W.powerlaw()
+    A, M = powerlaw
     b = W.rhs_ones(A)
-    M = bcs.csr_upload(A, stores=bcs.STORE_F32)
     for prec in ["fp32", "fp64"]:
         S = bcs.solver_create(M, "p-BiCGSafe-rr", tol=1e-10, maxit=20000, precision=prec, max_outer=30)
         bd = torch.from_numpy(b).cuda()
