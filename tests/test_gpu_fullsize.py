@@ -294,6 +294,38 @@ def test_cd3d27_192_full_solve_true_residual(env, cd3d27, kind, prec, layout):
 
 # ---- 512 independent 2D systems, sides 32..256, in one persistent launch -------------------------
 
+GOLDENB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch_cd2d_512_solves.json")
+
+
+def test_batch_cd2d_512_fp64_matches_oracle(env):
+    """The full 512-system FP64 batch in the configuration bench.py times (one launch, one lane
+    per row, clusters of two CTAs, replacement every 20 iterations) against the oracle's solve of
+    every system (tests/golden/batch_cd2d_512_solves.json, written by
+    make_batch_cd2d_512_solves.py from oracle/ alone): for each system the same iterations,
+    outer runs and replacement steps, the same true residual and x, bit for bit."""
+    bcs, torch, orc = env
+    with open(GOLDENB) as fh:
+        gold = json.load(fh)
+    o = gold["options"]
+    mats, sides, betas = W.batch_cd2d()
+    Ms = [bcs.csr_upload(A) for A in mats]
+    bs = [W.rhs_ones(A) for A in mats]
+    assert [_sha(b) for b in bs] == [g["b_sha256"] for g in gold["systems"]]
+    bd = [torch.from_numpy(b).cuda() for b in bs]
+    xd = [torch.zeros_like(b) for b in bd]
+    worst, res = bcs.solve_batched(Ms, bd, xd, kind=gold["kind"], tol=o["tol"], maxit=o["maxit"], precision="fp64",
+                                   max_outer=o["max_runs"], rr_m=o["rr_m"], rr_M=o["rr_M"])
+    assert worst == 0
+    bad = []
+    for k, (g, r, x) in enumerate(zip(gold["systems"], res, xd)):
+        same = (g["status"] == "ok" and r["status"] == bcs.OK and r["iterations"] == g["iterations"] and
+                r["outer_steps"] == g["outer_steps"] and r["rr_steps"] == g["rr_steps"] and
+                r["rel_res_true"] == float.fromhex(g["rel_res_true"]) and _sha(x.cpu().numpy()) == g["x_sha256"])
+        if not same:
+            bad.append((k, g["n"], g["iterations"], r["iterations"]))
+    assert not bad, bad
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_batch_cd2d_512_true_residuals(env, prec):
     """The full 512-system batch in the configuration bench.py times (default batched options,
