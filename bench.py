@@ -32,6 +32,9 @@ METRIC = "time to 1e-10 rel. residual, pipelined vs plain; HBM GB/s per iter; so
 HBM_PEAK_FALLBACK = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal; the FP64 units also bound the FP64 kernel)
 GOLDEN = os.path.join(ROOT, "tests", "golden", "cd3d128_full_solves.json")
+# the oracle's complete FP64 solves of the side workloads (tests/golden/make_*_solves.py)
+SIDE_GOLDEN = {"powerlaw_4m": "powerlaw_4m_full_solves.json", "cd3d27_192": "cd3d27_192_full_solves.json",
+               "cd3d_128_pc": "cd3d128_full_solves.json", "batch_cd2d_512": "batch_cd2d_512_solves.json"}
 
 
 # DRAM traffic of the solve kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on this
@@ -175,6 +178,53 @@ def error_vs_oracle(x, kind, gold):
     return {"oracle_kind": kind, "max_abs_err_sampled": float(np.max(np.abs(x[rows] - ref))),
             "sampled_rows": len(rows), "bit_identical": x_sha256(x) == g["x_sha256"],
             "oracle_iterations": g["iterations"], "oracle_outer_steps": g["outer_steps"]}
+
+
+def error_vs_oracle_side(x, kind, n, gold):
+    """error_vs_oracle for a side workload's returned x against the golden file's oracle solve of
+    this system: by the same method when the file holds it, else by the first of p-BiCGSafe-rr,
+    ssBiCGSafe2 and p-BiCGSafe that it holds (every one solved the system to 1e-10; oracle_kind
+    says which)."""
+    if gold is None or gold.get("n") != n:
+        return None
+    solves = gold.get("solves", {})
+    ref = kind if kind in solves else next((k for k in ("p-BiCGSafe-rr", "ssBiCGSafe2", "p-BiCGSafe")
+                                            if k in solves), None)
+    return None if ref is None else error_vs_oracle(x, ref, gold)
+
+
+def side_golden(workload):
+    """The golden file of a side workload (the oracle's solves), or None."""
+    f = SIDE_GOLDEN.get(workload)
+    path = os.path.join(ROOT, "tests", "golden", f) if f else None
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def batch_sample_rows(n, k):
+    """k evenly spaced rows of an n-row system, the first and the last included (the rows whose
+    x values the batch golden file records)."""
+    return np.unique(np.linspace(0, n - 1, k).round().astype(np.int64))
+
+
+def batch_error_vs_oracle(xs, which, gold):
+    """Error of the returned x of batched systems against the FP64 oracle's x of the same system
+    (the golden file's method, named in oracle_kind): max |x - x_oracle| over the file's sampled
+    rows of every system, and how many systems are bit-identical.  xs[j] is system which[j] of the
+    batch (host arrays)."""
+    if gold is None:
+        return None
+    err, same = 0.0, 0
+    k = gold["samples_per_system"]
+    for x, s in zip(xs, which):
+        g = gold["systems"][s]
+        ref = np.array([float.fromhex(v) for v in g["x_sample"]])
+        err = max(err, float(np.max(np.abs(x[batch_sample_rows(len(x), k)] - ref))))
+        same += x_sha256(x) == g["x_sha256"]
+    return {"oracle_kind": gold["kind"], "systems_checked": len(which), "bit_identical_systems": same,
+            "max_abs_err_sampled": err, "sampled_rows_per_system": k}
 
 
 def oracle_check_small(bcs, torch):
@@ -399,6 +449,8 @@ def side_single(a, bcs, torch, dist, world, rank):
             "ms_per_solve": t * 1e3, "iterations": res["iterations"], "outer_steps": res["outer_steps"],
             "us_per_iter": t * 1e6 / max(1, res["iterations"]), "status": res["status_name"],
             "rel_res_true": res["rel_res_true"],
+            "error_vs_oracle": None if a.matrix else error_vs_oracle_side(xd.cpu().numpy(), a.kind, A.n,
+                                                                         side_golden(a.workload)),
             "config": {"workload": ("Matrix Market file %s" % os.path.basename(a.matrix)) if a.matrix else
                        "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "n": A.n, "nnz": A.nnz,
                        "kind": a.kind, "precision": a.precision, "layout": layout, "threads_per_row": tpr,
@@ -448,6 +500,7 @@ def side_batch(a, bcs, torch, dist, world, rank):
             "systems": 512, "systems_this_rank": len(mats), "converged_this_rank": ok, "worst_status": code,
             "iterations": {"min": min(its), "median": float(np.median(its)), "max": max(its)},
             "max_rel_res_true": max(r["rel_res_true"] for r in res),
+            "error_vs_oracle": batch_error_vs_oracle([x.cpu().numpy() for x in xs], mine, side_golden(a.workload)),
             "per_system_ms": {"median": spans[len(spans) // 2][0], "max": spans[-1][0], "max_n": spans[-1][1],
                               "last_finish": ends[-1], "p90_finish": ends[int(0.9 * (len(ends) - 1))]},
             "config": {"workload": "%s: %s" % (a.workload, SIDE_WORKLOADS[a.workload]), "kind": a.kind,

@@ -12,8 +12,9 @@ system per task, with the oracle's single-threaded parity build:
     python tests/golden/make_batch_cd2d_512_solves.py
 
 Recorded per system: side, n, status, iterations (summed over the runs), outer
-runs, replacement steps, the relative true residual and SHA-256 digests of b
-and of the returned x (little-endian FP64 bytes).
+runs, replacement steps, the relative true residual, SHA-256 digests of b and
+of the returned x (little-endian FP64 bytes), and x at 16 evenly spaced rows
+(hex floats; the rows are sample_rows(n)).
 """
 import hashlib
 import json
@@ -33,8 +34,16 @@ KIND = "p-BiCGSafe-rr"
 OPTIONS = {"tol": 1e-10, "maxit": 10000, "max_runs": 30, "rr_m": 20, "rr_M": 10001}
 
 
+NSAMPLE = 16
+
+
 def digest(a):
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<f8").tobytes()).hexdigest()
+
+
+def sample_rows(n, k=NSAMPLE):
+    """k evenly spaced rows of an n-row system, the first and the last included."""
+    return np.unique(np.linspace(0, n - 1, k).round().astype(np.int64))
 
 
 _BATCH = {}
@@ -53,7 +62,8 @@ def solve_one(k):
                      rr_M=OPTIONS["rr_M"], max_restarts=OPTIONS["max_runs"] - 1, hist_cap=16)
     return {"side": int(sides[k]), "n": int(A.n), "status": r["status_name"], "iterations": r["iterations"],
             "outer_steps": r["restarts"] + 1, "rr_steps": r["rr_steps"],
-            "rel_res_true": float(r["rel_res_true"]).hex(), "b_sha256": digest(b), "x_sha256": digest(r["x"])}
+            "rel_res_true": float(r["rel_res_true"]).hex(), "b_sha256": digest(b), "x_sha256": digest(r["x"]),
+            "x_sample": [float(v).hex() for v in r["x"][sample_rows(A.n)]]}
 
 
 def main():
@@ -61,7 +71,8 @@ def main():
     with mp.get_context("spawn").Pool(os.cpu_count() or 4) as pool:
         systems = pool.map(solve_one, range(512), chunksize=4)
     out = {"workload": "batch_cd2d_512: 512 cd2d systems, side U{32..256}, beta U[0,50], b=A*1, x0=0",
-           "kind": KIND, "options": OPTIONS, "systems": systems, "oracle_seconds": round(time.time() - t0, 1)}
+           "kind": KIND, "options": OPTIONS, "samples_per_system": NSAMPLE, "systems": systems,
+           "oracle_seconds": round(time.time() - t0, 1)}
     with open(OUT, "w") as fh:
         json.dump(out, fh, indent=0)
         fh.write("\n")

@@ -56,3 +56,47 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("cd3d_16:")
+
+
+def _load(path):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_golden_maker", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_side_lines_state_error_against_the_oracle_golden_files():
+    """The side lines' error_vs_oracle reads the oracle's golden solves: the sampled rows of the
+    batch file are the ones its generator recorded, an x that carries the oracle's values at the
+    sampled rows has zero sampled error (but is not bit-identical), a method that the file lacks is
+    compared with the file's p-BiCGSafe-rr solve, and another system size gives no comparison."""
+    import numpy as np
+    here = os.path.dirname(os.path.abspath(__file__))
+    maker = _load(os.path.join(here, "golden", "make_batch_cd2d_512_solves.py"))
+    for n in (1024, 4096, 30625, 65536):
+        assert np.array_equal(bench.batch_sample_rows(n, maker.NSAMPLE), maker.sample_rows(n))
+
+    gold = bench.side_golden("batch_cd2d_512")
+    which = [0, 7, 511]
+    xs = []
+    for s in which:
+        g = gold["systems"][s]
+        x = np.zeros(g["n"])
+        x[bench.batch_sample_rows(g["n"], gold["samples_per_system"])] = [float.fromhex(v) for v in g["x_sample"]]
+        xs.append(x)
+    e = bench.batch_error_vs_oracle(xs, which, gold)
+    assert e["max_abs_err_sampled"] == 0.0 and e["bit_identical_systems"] == 0 and e["systems_checked"] == 3
+    xs[1][bench.batch_sample_rows(len(xs[1]), gold["samples_per_system"])[3]] += 0.5
+    assert bench.batch_error_vs_oracle(xs, which, gold)["max_abs_err_sampled"] == pytest.approx(0.5, abs=1e-12)
+
+    pl = bench.side_golden("powerlaw_4m")
+    rows = np.asarray(pl["sample_rows"])
+    x = np.zeros(pl["n"])
+    x[rows] = [float.fromhex(v) for v in pl["solves"]["ssBiCGSafe2"]["x_sample"]]
+    e = bench.error_vs_oracle_side(x, "ssBiCGSafe2", pl["n"], pl)
+    assert e["max_abs_err_sampled"] == 0.0 and not e["bit_identical"]
+    assert bench.error_vs_oracle_side(x, "ssBiCGSafe2", pl["n"] - 1, pl) is None
+    e = bench.error_vs_oracle_side(x, "GPBiCG", pl["n"], pl)   # a method the file lacks: its first solve
+    assert e["oracle_kind"] == "p-BiCGSafe-rr" and e["max_abs_err_sampled"] > 0.0
+    assert bench.side_golden("no_such_workload") is None
